@@ -1,0 +1,95 @@
+"""Solve and post-process (Secs. 2.1 and 2.3).
+
+* ``solve``: the linear system A u = b of Eq. (matrix_eqn), solved directly
+  (sparse LU) so that the oracle has no iteration error.
+* ``layer_energies``: U = -1/2 int S_ij T^ij dV with T = -Y S (Sec. 2.1),
+  i.e. 1/2 int S : Y : S, evaluated per material layer with the element's own
+  (unlifted) strain S = D_(k u_l) at its LGL nodes and LGL weights.
+* ``noise_psd``: the fluctuation-dissipation relation, Eq. (thermalnoise),
+  with the quasistatic loss of Eq. (wdiss) summed over layers.  Taken as a
+  dissipated power (energy per cycle 2 pi U phi, times f) this reads
+  S_q = 4 k_B T sum_i phi_i U_i / (pi f F0^2); only this constant is a
+  reading, S_q proportional to sum_i phi_i U_i is the paper's.
+* ``half_space_energy``: closed-form energy of an isotropic half-space under
+  the pressure profile of Eq. (laserbeam), (1 - nu^2) F0^2 / (2 sqrt(2 pi) Y r0),
+  and the same number by quadrature of the Boussinesq surface response.
+
+Test infrastructure: slow, plain FP64, imported only by tests and by the
+CPU-baseline leg of the benchmark.
+"""
+import math
+
+import numpy as np
+import scipy.sparse.linalg as spla
+from scipy import integrate, special
+
+BOLTZMANN = 1.380649e-23
+
+
+def solve(A, b):
+    return spla.splu(A.tocsc()).solve(b)
+
+
+def element_energy(op, e, u):
+    mesh = op.mesh
+    n, nloc = mesh.n, 3 * mesh.n
+    ue = u[e * nloc:(e + 1) * nloc].reshape(3, n)
+    G = op.grad_matrices(e)
+    grad = np.stack([G[a] @ ue.T for a in range(3)], axis=1)  # (n, a, l) = du_l/dx^a
+    S = 0.5 * (grad + grad.transpose(0, 2, 1))
+    dens = np.einsum("pij,ijkl,pkl->p", S, op.Ye(e), S)
+    return 0.5 * float(np.sum(mesh.geometry(e)["wJ"] * dens))
+
+
+def layer_energies(op, u):
+    """U_i per layer id (coating layers top-down, the substrate last)."""
+    U = np.zeros(op.mesh.n_layers)
+    for e in range(op.mesh.E):
+        U[op.mesh.layer(e)] += element_energy(op, e, u)
+    return U
+
+
+def noise_psd(U, phi, kB_T, f, F0):
+    return 4.0 * kB_T * float(np.dot(phi, U)) / (math.pi * f * F0 ** 2)
+
+
+def half_space_energy(Y, nu, F0, r0):
+    return (1.0 - nu ** 2) * F0 ** 2 / (2.0 * math.sqrt(2.0 * math.pi) * Y * r0)
+
+
+def half_space_energy_quadrature(Y, nu, F0, r0):
+    """U = (1 - nu^2) / (2 pi Y) int_0^inf |p_hat(k)|^2 dk, from the surface
+    response w_hat = 2 (1 - nu^2) p_hat / (Y k) of a half-space, with p_hat
+    the Hankel transform of F0 p(r) computed by quadrature."""
+    def p(r):
+        return F0 * math.exp(-r * r / r0 ** 2) / (math.pi * r0 ** 2)
+
+    def p_hat(k):
+        val, _ = integrate.quad(lambda r: 2 * math.pi * r * p(r) * special.j0(k * r),
+                                0.0, 12.0 * r0, limit=200)
+        return val
+
+    val, _ = integrate.quad(lambda k: p_hat(k) ** 2, 0.0, 16.0 / r0, limit=200)
+    return (1.0 - nu ** 2) / (2.0 * math.pi * Y) * val
+
+
+def solve_cg(op, A, b, rtol=1e-12, maxiter=20000):
+    """A u = b by conjugate gradients preconditioned with the exact inverse of
+    each element's diagonal block: the oracle's iterative solve for systems
+    too large to factor (its result carries the iteration error rtol)."""
+    import scipy.sparse as sp
+    nl = 3 * op.mesh.n
+    blocks = [sp.csr_matrix(np.linalg.inv(A[e * nl:(e + 1) * nl, e * nl:(e + 1) * nl].toarray()))
+              for e in range(op.mesh.E)]
+    Minv = sp.block_diag(blocks, format="csr")
+    u, info = spla.cg(A, b, rtol=rtol, atol=0.0, M=Minv, maxiter=maxiter)
+    if info != 0:
+        raise RuntimeError(f"oracle CG did not converge (info={info})")
+    return u
+
+
+def solve_dense(A, b):
+    """A u = b by dense Cholesky (fails loudly if A is not positive definite)."""
+    import scipy.linalg as sl
+    c = sl.cho_factor(A.toarray(), lower=True, overwrite_a=True, check_finite=False)
+    return sl.cho_solve(c, b)
