@@ -1,0 +1,376 @@
+"""Benchmark of the DG thermal-noise hot path on GB300.
+
+One step = one pass of the whole path on the 2.0 M DOF single-coating
+mirror (cylinder R = H = 10 r0, 0.02 r0 coating, p = 6): right-hand side,
+Jacobi diagonal, mixed-precision solve (FP32 inner PCG, FP64 residual and
+refinement) until every layer energy is within 1e-9 of the FP64 reference,
+per-layer energies and the noise PSD.  Inputs (mesh, geometry, materials)
+are resident in HBM before the timed region; L2 is flushed between steps.
+
+metric: GDOF/s = (operator applies x N_DOF) / time, over the whole step.
+Extra keys report the FP32/FP64 apply kernels alone, the time to U for the
+mixed and the plain FP64 solve, the roofline of the dominant kernel and the
+FP64 oracle on the host cores.
+
+Multi-GPU: replicas only (every rank solves its own mirror; no collective on
+the data path); value = all ranks' DOF-applies / max over ranks of the time.
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "single_coating": W.single_coating,
+    "plain_box": W.plain_box,
+    "crystalline_multilayer": W.crystalline_multilayer,
+    "large_mirror": W.large_mirror,
+}
+KB_T = 1.380649e-23 * 300.0
+FREQ = 100.0
+
+
+def fp32_apply_flops_per_dof(N):
+    """Algorithmic FP32 work of one operator apply per DOF: the sum-factorised
+    gradient and weak divergence (36 N flops per node), metric / strain /
+    stress / flux transforms (~80 per node), and per face node (6 N^2 per
+    element) the neighbour normal and tangential derivatives plus the flux
+    terms (~130 + 18 N)."""
+    per_elem = N ** 3 * (36 * N + 80) + 6 * N ** 2 * (130 + 18 * N)
+    return per_elem / (3 * N ** 3)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample_rate(desc, budget_s, max_elems=64):
+    """The FP64 oracle's apply on a bounded sample of the same workload:
+    element rows of A u built from explicit element matrices, as it stands.
+    Returns (GDOF/s, elements sampled, seconds, threads)."""
+    from oracle import Mesh, Operator
+    m = Mesh(desc)
+    op = Operator(m)
+    u = W.random_field(desc, 0)
+    rng = np.random.default_rng(1)
+    elems = rng.permutation(m.E)[:max_elems]
+    t0 = time.perf_counter()
+    done = 0
+    for e in elems:
+        op.apply_element(int(e), u)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            threads = max(i.get("num_threads", 1) for i in info)
+    except ImportError:
+        pass
+    return done * 3 * m.n / dt / 1e9, done, dt, threads
+
+
+def run_reference(args, desc, world, rank):
+    if rank != 0:
+        return
+    times = []
+    dofs = 0
+    for it in range(args.warmup + args.steps):
+        rate, done, dt, threads = oracle_sample_rate(desc, budget_s=args.ref_step_s)
+        if it >= args.warmup:
+            times.append(dt)
+            dofs += rate * dt * 1e9
+    total = sum(times)
+    value = dofs / total / 1e9
+    N = desc["degree"] + 1
+    line = {
+        "impl": "reference", "metric": "GDOF/s of DG elasticity apply", "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "ndof": W.n_dof(desc), "degree": desc["degree"],
+                   "elements": W.n_elements(desc)},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+                         "sample": f"FP64 oracle element rows of A u (explicit element matrices, N={N}) "
+                                   f"for up to {args.ref_step_s:.0f} s of elements per step"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single_coating", choices=sorted(WORKLOADS))
+    ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-U solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    desc = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        run_reference(args, desc, world, rank)
+        return
+
+    import torch
+    from paper_2111_06893_gb300 import build, thermonoise
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        build.build()
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = thermonoise.setup(desc, device=local, stream=stream)
+    ndof = ctx.ndof
+    N = desc["degree"] + 1
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # FP64 reference energies (GPU FP64 solve to 1e-13) and its time to U
+    u_ref, rep_ref = ctx.solve(mode="f64", rtol=1e-13)
+    U_ref = ctx.layer_energies(u_ref)
+    t_fp64 = None
+    rep_fp64 = None
+    if not args.no_fp64:
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u64, rep_fp64 = ctx.solve(mode="f64", rtol=args.rtol)
+        U64 = ctx.layer_energies(u64)
+        torch.cuda.synchronize()
+        t_fp64 = time.perf_counter() - t0
+        err64 = float(np.max(np.abs(U64 - U_ref) / U_ref))
+        del u64
+
+    phi = np.array([4e-4] * (len(desc["materials"]) - 1) + [1e-6])
+    u = torch.empty(ndof, dtype=torch.float64, device=dev)
+
+    def step():
+        _, rep = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u)
+        U = ctx.layer_energies(u)
+        S = thermonoise.noise_psd(U, phi, KB_T, FREQ, desc["beam"]["F0"])
+        return rep, U, S
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, applies, launches = 0.0, 0, 0
+    reps = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(float(len(reps)))
+            ev0.record(stream)
+            rep, U, S = step()
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            applies += rep["applies_f32"] + rep["applies_f64"]
+            launches += rep["launches"] + 2
+            reps.append(rep)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    err_mixed = float(np.max(np.abs(U - U_ref) / U_ref))
+    t_local = total_ms / 1e3
+    t_max = t_local
+    tot_applies = applies
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        aa = torch.tensor([applies], dtype=torch.float64, device=dev)
+        dist.all_reduce(aa, op=dist.ReduceOp.SUM)
+        tot_applies = float(aa.item())
+    value = tot_applies * ndof / t_max / 1e9
+    mixed_s = t_local / args.steps
+
+    # ---- the dominant kernel alone: FP32 and FP64 applies, CUDA events on the launch stream
+    x32 = torch.rand(ndof, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(x32)
+    x64 = x32.double()
+    y64 = torch.empty_like(x64)
+
+    def time_apply(x, y, reps_n):
+        for _ in range(5):
+            ctx.apply_operator(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps_n):
+            ctx.apply_operator(x, y)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps_n / 1e3
+
+    t32 = time_apply(x32, y32, 200)
+    t64 = time_apply(x64, y64, 20)
+    flops = fp32_apply_flops_per_dof(N) * ndof
+    sm_max = 2070.0
+    peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
+    achieved = flops / t32 / 1e12
+    peaks = measured_peaks()
+
+    # ---- end to end through the C ABI with host buffers
+    u_host = torch.empty(ndof, dtype=torch.float64, pin_memory=True)
+    ncol = W.n_columns(desc)
+    nslab = len(desc["slab_z"]) - 1
+    h2d = ncol * (7 * N * N * 8 + 8 * 4) + nslab * (2 * N * 8 + 4) + len(desc["materials"]) * 24
+    d2h = ndof * 8 + len(desc["materials"]) * 8
+    e2e_times = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.build_mesh(desc)
+        ctx.set_materials(desc["materials"])
+        ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
+        _, rep_e = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u)
+        u_host.copy_(u, non_blocking=True)
+        U_e = ctx.layer_energies(u)
+        thermonoise.noise_psd(U_e, phi, KB_T, FREQ, desc["beam"]["F0"])
+        torch.cuda.synchronize()
+        e2e_times.append((time.perf_counter() - t0, rep_e["applies_f32"] + rep_e["applies_f64"]))
+    e2e_value = e2e_times[-1][1] * ndof / e2e_times[-1][0] / 1e9
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        rate, done, dt, threads = oracle_sample_rate(desc, budget_s=args.cpu_budget_s)
+        cpu = {"value": rate, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+               "sample": f"{done} element rows of A u of this workload by the FP64 oracle "
+                         f"(explicit element matrices), {dt:.1f} s"}
+    clocks = clk.summary()
+    line = {
+        "metric": "GDOF/s of DG elasticity apply", "value": value, "unit": "GDOF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "ndof": ndof, "degree": desc["degree"],
+                   "elements": W.n_elements(desc), "step": "rhs+diag+mixed solve+energies+psd",
+                   "rtol": args.rtol, "inner_rtol": args.inner_rtol, "l2": "flushed between steps (256 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "time_to_U_s": {"mixed": mixed_s, "fp64": t_fp64,
+                        "mixed_energy_rel_err": err_mixed,
+                        "fp64_energy_rel_err": err64 if t_fp64 is not None else None},
+        "solve": {"inner_iters": reps[-1]["inner_iters"], "outer_iters": reps[-1]["outer_iters"],
+                  "applies_f32": reps[-1]["applies_f32"], "applies_f64": reps[-1]["applies_f64"],
+                  "rel_residual": reps[-1]["rel_residual"],
+                  "fp64_iters": rep_fp64["inner_iters"] if rep_fp64 else None},
+        "apply_kernel": {"f32_us": t32 * 1e6, "f64_us": t64 * 1e6,
+                         "f32_gdofs": ndof / t32 / 1e9, "f64_gdofs": ndof / t64 / 1e9},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None,
+                     "kernel": f"apply_kernel<{N},float>",
+                     "flops_per_dof": fp32_apply_flops_per_dof(N),
+                     "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
+                     "hbm_peak_GBps": peaks.get("hbm_gbs"),
+                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "seconds": e2e_times[-1][0]},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

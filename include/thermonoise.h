@@ -1,0 +1,184 @@
+/*
+ * thermonoise.h -- C ABI of the GB300 (sm_103a) library for the discontinuous
+ * Galerkin model of Brownian coating thermal noise (arXiv 2111.06893).
+ *
+ * The library applies the matrix-free internal-penalty DG operator of static
+ * linear elasticity (Sec. 2.2), solves it for the Gaussian-beam load
+ * (Sec. 2.1, Eq. (laserbeam); Sec. 2.3, Eq. (matrix_eqn)), reduces the
+ * solution to per-layer elastic energies (Sec. 2.1, potential energy and its
+ * decomposition by layer) and evaluates the noise PSD (Eq. (thermalnoise)).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns tn_status; TN_OK == 0, errors are negative.
+ *     No exception crosses the ABI.  tn_last_error() returns a thread-local,
+ *     NUL-terminated description of the last failure on the calling thread.
+ *   - Arguments are validated before any GPU work (TN_EINVAL).
+ *   - Pointers named *_dev are device pointers owned by the caller (for
+ *     example a torch tensor's data_ptr); pointers named *_host are host
+ *     memory owned by the caller.  The context owns the mesh, geometry and
+ *     solver workspace it allocates and frees them in tn_destroy().
+ *   - Work is queued on the context's CUDA stream (given to tn_create) and is
+ *     asynchronous, except where a function returns host data (then it
+ *     synchronises that stream before returning).
+ *   - One context per host thread at a time.
+ *
+ * Field layout (all device vectors): element-major, component-blocked,
+ *   u[(e * 3 + c) * N^3 + (k * N + j) * N + i],  N = degree + 1,
+ * with (i, j, k) the LGL node indices along the element's logical axes
+ * (xi, eta, zeta), c the Cartesian component (x, y, z).  Elements are
+ * numbered e = s * n_columns + col: slab s counted from the top surface z = 0
+ * downwards, col the cross-section column (box: col = jy * nx + ix;
+ * cylinder: nine blocks [square, inner wedges at 0/90/180/270 degrees, outer
+ * wedges at 0/90/180/270 degrees], col = block * k^2 + b * k + a inside a
+ * block split k x k).
+ */
+#ifndef THERMONOISE_H
+#define THERMONOISE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_EINVAL = -1,     /* invalid argument; nothing was launched            */
+  TN_ENOMEM = -2,     /* device or host allocation failed                  */
+  TN_ECUDA = -3,      /* a CUDA call failed (text in tn_last_error)        */
+  TN_ENOTCONV = -4,   /* iteration limit reached; best iterate returned    */
+  TN_EBREAKDOWN = -5, /* Krylov breakdown (p.Ap <= 0 or not finite)        */
+  TN_ETIMEOUT = -6,   /* a bounded device wait gave up                     */
+  TN_ESTATE = -7      /* call out of order (e.g. no mesh built yet)        */
+} tn_status;
+
+enum { TN_MESH_BOX = 0, TN_MESH_CYLINDER = 1 };
+enum { TN_BC_FREE = 0, TN_BC_FIXED = 1 };
+enum { TN_F64 = 0, TN_F32 = 1 };
+enum { TN_ISO = 0, TN_CUBIC = 1 };
+enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED_F32 = 1 };
+enum { TN_PC_JACOBI = 0 };
+
+typedef struct tn_ctx tn_ctx;
+
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Uploads the LGL tables to the device.  Returns TN_ECUDA if the
+ * device cannot be used. */
+tn_status tn_create(tn_ctx **out, int device, void *cuda_stream);
+/* Free everything the context owns.  NULL is accepted. */
+void tn_destroy(tn_ctx *ctx);
+/* Text of the last failure on this thread ("" if none). */
+const char *tn_last_error(void);
+
+/* Mesh description (Sec. 2.2.1, Fig. 1).  The cross-section is a box split
+ * along x and y, or a disk of radius R made of a central square [-a, a]^2,
+ * four wedges from the square to the circle of radius R1 and four outer
+ * wedges to R, each of the nine blocks split k x k.  Vertically the domain is
+ * cut into n_slabs slabs listed from the top (slab_z[0] = 0) downwards; slab s
+ * spans slab_z[s+1] < z < slab_z[s], belongs to layer slab_layer[s] and uses a
+ * logarithmic map in depth -z if slab_log[s] != 0 (then slab_z[s] < 0).
+ * Layer interfaces therefore coincide with element boundaries (Sec. 4).
+ * The top z = 0 carries the beam pressure (Neumann, Eq. (bc)); the sides /
+ * mantle and the bottom are TN_BC_FIXED (u = 0, Eq. (BCfixed)) or
+ * TN_BC_FREE (zero traction, Eq. (BCfree)).  The penalty is
+ * sigma = penalty_C (degree + 1)^2 / h (Eq. (penalty)).  degree in 2..8. */
+typedef struct {
+  int kind;                 /* TN_MESH_BOX or TN_MESH_CYLINDER             */
+  int degree;               /* polynomial degree p; N = p + 1 LGL points   */
+  int nx, ny;               /* box: elements along x and y                 */
+  const double *x_breaks;   /* box: nx + 1 increasing x values (host)      */
+  const double *y_breaks;   /* box: ny + 1 increasing y values (host)      */
+  double R, a, R1;          /* cylinder radii, 0 < a < R1 < R              */
+  int k;                    /* cylinder: k x k split of each block         */
+  int n_slabs;              /* >= 1                                        */
+  const double *slab_z;     /* n_slabs + 1 decreasing z values, [0] == 0   */
+  const int *slab_layer;    /* n_slabs layer ids in [0, n_layers)          */
+  const int *slab_log;      /* n_slabs flags                               */
+  int n_layers;             /* coating layers + substrate                  */
+  double penalty_C;         /* > 0                                         */
+  int bc_side, bc_bottom;   /* TN_BC_FREE or TN_BC_FIXED                   */
+} tn_mesh_desc;
+
+/* Build the mesh and its geometry (FP64) on the device; replaces any earlier
+ * mesh of the context.  Host arrays are copied; the caller keeps ownership. */
+tn_status tn_build_mesh(tn_ctx *ctx, const tn_mesh_desc *desc);
+
+/* Number of unknowns N_DOF = 3 * N^3 * n_elements (Sec. 2.3). */
+tn_status tn_ndof(const tn_ctx *ctx, int64_t *ndof);
+
+/* Material of each layer (Sec. 2.1): TN_ISO from Young's modulus Y and
+ * Poisson ratio nu (Eq. (constrel_iso) and its footnote), or TN_CUBIC with
+ * c11, c12, c44 and crystal axes along x, y, z (Eq. (constrel_cryst)).
+ * n must equal the mesh's n_layers; layer n-1 is the substrate. */
+typedef struct {
+  int kind;
+  double Y, nu;
+  double c11, c12, c44;
+} tn_material;
+tn_status tn_set_materials(tn_ctx *ctx, int n, const tn_material *m);
+
+/* Gaussian beam p(r) = F0 exp(-r^2/r0^2) / (pi r0^2) (Eq. (laserbeam)),
+ * centred on the z axis. r0 > 0. */
+tn_status tn_set_beam(tn_ctx *ctx, double r0, double F0);
+
+/* y = A u: one application of the DG operator of Eq. (dg_residuals) (weak
+ * form, homogeneous boundary data).  precision TN_F64: u, y are double;
+ * TN_F32: float (geometry is kept in FP64 and rounded per node).  u and y
+ * are caller-owned device buffers of tn_ndof() elements, must not overlap,
+ * and must be 16-byte aligned. */
+tn_status tn_apply_operator(tn_ctx *ctx, int precision, const void *u_dev, void *y_dev);
+
+/* b of A u = b (Eq. (matrix_eqn)) for the beam load: b = -sum over top-face
+ * nodes of w^S J^S p(r) e_z (Neumann data of Eq. (bc)).  FP64, ndof values. */
+tn_status tn_rhs(tn_ctx *ctx, double *b_dev);
+
+/* diag(A) in FP64 (the Jacobi preconditioner). ndof values. */
+tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
+
+/* Krylov solve of A u = b for the beam load (Sec. 2.3).
+ * mode TN_SOLVE_F64: Jacobi-preconditioned CG in FP64.
+ * mode TN_SOLVE_MIXED_F32: iterative refinement, FP64 residual b - A x and
+ * update, inner Jacobi-PCG entirely in FP32 to inner_rtol.
+ * Stops when ||b - A u||_2 <= rtol ||b||_2 (FP64 residual).  u_dev holds the
+ * initial guess on entry if use_x0 != 0 (else it starts from 0) and the FP64
+ * solution on exit.  Returns TN_ENOTCONV with the best iterate if max_iter
+ * (total inner iterations) is reached. */
+typedef struct {
+  int mode;
+  int precond;
+  double rtol;
+  double inner_rtol;
+  int max_iter;
+  int max_outer;
+  int use_x0;
+  int check_every;          /* iterations between host convergence checks */
+} tn_solve_opts;
+typedef struct {
+  int status;
+  int outer_iters;
+  int inner_iters;
+  int applies_f64;
+  int applies_f32;
+  int64_t launches;         /* kernel launches issued by this call         */
+  double rel_residual;
+  double seconds;
+} tn_solve_report;
+tn_status tn_solve(tn_ctx *ctx, const tn_solve_opts *opts, double *u_dev, tn_solve_report *rep);
+
+/* Per-layer elastic energy U_i = 1/2 sum_{e in layer i} sum_p w_p detJ_p
+ * S_p : Y : S_p with S = sym grad u at the element's own nodes (Sec. 2.1,
+ * U = -1/2 int S_ij T^ij dV, T = -Y S).  u_dev: FP64 field; U_host receives
+ * n_layers doubles (coating layers top-down, substrate last).  Synchronises. */
+tn_status tn_layer_energies(tn_ctx *ctx, const double *u_dev, double *U_host);
+
+/* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
+ * per layer, dissipated power 2 pi f sum_i phi_i U_i):
+ *   S_out = 4 kB_T sum_i phi_i U_i / (pi f F0^2).  Host only. */
+tn_status tn_noise_psd(const double *U_host, const double *phi_host, int n, double kB_T,
+                       double f, double F0, double *S_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THERMONOISE_H */

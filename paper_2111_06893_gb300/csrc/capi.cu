@@ -1,0 +1,420 @@
+// C ABI of the thermonoise library (declared in include/thermonoise.h):
+// context and workspace management, argument validation, and the host-side
+// orchestration of the solve, energies and PSD.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "tn_internal.h"
+#include "tn_solver.h"
+
+namespace {
+thread_local char g_err[512] = "";
+
+tn_status fail(tn_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+tn_status cuda_fail(cudaError_t e, const char *where) {
+  return fail(TN_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CU_TRY(call, where)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+}  // namespace
+
+struct tn_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;   // the caller's stream
+  cudaStream_t sstream = nullptr;  // internal stream used for graph capture
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  tn::HostMesh hm;
+  bool have_mesh = false, have_mat = false, have_beam = false;
+  DevMesh dm{};
+  double *d_colgeo = nullptr, *d_slabgeo = nullptr, *d_layer_c = nullptr;
+  int *d_colnb = nullptr, *d_colnbf = nullptr, *d_slab_layer = nullptr;
+  double r0 = 1.0, F0 = 1.0;
+  size_t ndof = 0;
+  // workspace
+  size_t ws_ndof = 0;
+  double *b64 = nullptr, *diag64 = nullptr, *dinv64 = nullptr, *r64 = nullptr, *z64 = nullptr,
+         *p64 = nullptr, *q64 = nullptr;
+  float *dinv32 = nullptr, *b32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr,
+        *q32 = nullptr, *d32 = nullptr;
+  double *part_elem = nullptr, *part_red = nullptr, *sum_dev = nullptr;
+  tn_pcg_scalars *scal = nullptr, *scal_host = nullptr;
+  double *elem_energy = nullptr, *layer_energy = nullptr;
+  size_t ws_E = 0;
+  int ws_layers = 0;
+};
+
+static void free_mesh(tn_ctx *c) {
+  dfree(c->d_colgeo);
+  dfree(c->d_slabgeo);
+  dfree(c->d_colnb);
+  dfree(c->d_colnbf);
+  dfree(c->d_slab_layer);
+  tn::free_host_mesh(&c->hm);
+  c->have_mesh = false;
+}
+
+static void free_ws(tn_ctx *c) {
+  dfree(c->b64); dfree(c->diag64); dfree(c->dinv64); dfree(c->r64); dfree(c->z64); dfree(c->p64);
+  dfree(c->q64); dfree(c->dinv32); dfree(c->b32); dfree(c->r32); dfree(c->z32); dfree(c->p32);
+  dfree(c->q32); dfree(c->d32);
+  dfree(c->part_elem); dfree(c->part_red); dfree(c->sum_dev); dfree(c->scal);
+  dfree(c->elem_energy); dfree(c->layer_energy);
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  c->scal_host = nullptr;
+  c->ws_ndof = 0;
+  c->ws_E = 0;
+  c->ws_layers = 0;
+}
+
+static tn_status ensure_ws(tn_ctx *c) {
+  if (c->ws_ndof == c->ndof && c->ws_E == (size_t)c->dm.E && c->ws_layers == c->dm.n_layers) return TN_OK;
+  free_ws(c);
+  const size_t n = c->ndof;
+  const size_t d8 = n * sizeof(double), f4 = n * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void **)&c->b64, d8); A((void **)&c->diag64, d8); A((void **)&c->dinv64, d8);
+  A((void **)&c->r64, d8); A((void **)&c->z64, d8); A((void **)&c->p64, d8); A((void **)&c->q64, d8);
+  A((void **)&c->dinv32, f4); A((void **)&c->b32, f4); A((void **)&c->r32, f4); A((void **)&c->z32, f4);
+  A((void **)&c->p32, f4); A((void **)&c->q32, f4); A((void **)&c->d32, f4);
+  A((void **)&c->part_elem, sizeof(double) * c->dm.E);
+  A((void **)&c->part_red, sizeof(double) * 2 * tn::reduction_blocks());
+  A((void **)&c->sum_dev, sizeof(double) * 2);
+  A((void **)&c->scal, sizeof(tn_pcg_scalars));
+  A((void **)&c->elem_energy, sizeof(double) * c->dm.E);
+  A((void **)&c->layer_energy, sizeof(double) * c->dm.n_layers);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->scal_host, sizeof(tn_pcg_scalars));
+  if (e != cudaSuccess) {
+    free_ws(c);
+    cudaGetLastError();
+    return fail(TN_ENOMEM, "workspace allocation of %zu DOF failed: %s", n, cudaGetErrorString(e));
+  }
+  c->ws_ndof = n;
+  c->ws_E = c->dm.E;
+  c->ws_layers = c->dm.n_layers;
+  return TN_OK;
+}
+
+static tn_status need_ready(const tn_ctx *c, bool beam) {
+  if (!c) return fail(TN_EINVAL, "null context");
+  if (!c->have_mesh) return fail(TN_ESTATE, "no mesh: call tn_build_mesh first");
+  if (!c->have_mat) return fail(TN_ESTATE, "no materials: call tn_set_materials after tn_build_mesh");
+  if (beam && !c->have_beam) return fail(TN_ESTATE, "no beam: call tn_set_beam first");
+  return TN_OK;
+}
+
+extern "C" {
+
+const char *tn_last_error(void) { return g_err; }
+
+tn_status tn_create(tn_ctx **out, int device, void *cuda_stream) {
+  if (!out) return fail(TN_EINVAL, "out is null");
+  *out = nullptr;
+  int count = 0;
+  CU_TRY(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(TN_EINVAL, "device %d out of range (%d devices)", device, count);
+  CU_TRY(cudaSetDevice(device), "cudaSetDevice");
+  tn_ctx *c = new (std::nothrow) tn_ctx();
+  if (!c) return fail(TN_ENOMEM, "host allocation failed");
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    static LglTables tabs;
+    std::memset(&tabs, 0, sizeof(tabs));
+    for (int N = 2; N <= TN_MAX_N; ++N) {
+      double D[TN_MAX_N * TN_MAX_N];
+      tn::lgl(N, tabs.x[N], tabs.w[N], D);
+      std::memcpy(tabs.D[N], D, sizeof(double) * N * N);
+    }
+    e = tn_upload_lgl(&tabs);
+  }
+  if (e != cudaSuccess) {
+    tn_destroy(c);
+    return cuda_fail(e, "tn_create");
+  }
+  *out = c;
+  return TN_OK;
+}
+
+void tn_destroy(tn_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  free_ws(c);
+  free_mesh(c);
+  dfree(c->d_layer_c);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->sstream) cudaStreamDestroy(c->sstream);
+  delete c;
+}
+
+tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
+  if (!c || !d) return fail(TN_EINVAL, "null argument");
+  tn::HostMesh hm;
+  char msg[256] = "";
+  tn_status st = tn::build_host_mesh(d, &hm, msg, sizeof(msg));
+  if (st != TN_OK) return fail(st, "tn_build_mesh: %s", msg);
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  CU_TRY(cudaStreamSynchronize(c->stream), "sync before rebuilding the mesh");
+  free_mesh(c);
+  free_ws(c);
+  dfree(c->d_layer_c);
+  c->have_mat = false;
+  c->hm = hm;
+  const int N2 = hm.N * hm.N;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void **dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up((void **)&c->d_colgeo, hm.colgeo, sizeof(double) * (size_t)hm.ncol * CG_NF * N2);
+  up((void **)&c->d_slabgeo, hm.slabgeo, sizeof(double) * (size_t)hm.nslab * SG_NF * hm.N);
+  up((void **)&c->d_colnb, hm.colnb, sizeof(int) * 4 * hm.ncol);
+  up((void **)&c->d_colnbf, hm.colnbf, sizeof(int) * 4 * hm.ncol);
+  up((void **)&c->d_slab_layer, hm.slab_layer, sizeof(int) * hm.nslab);
+  if (e != cudaSuccess) {
+    free_mesh(c);
+    return cuda_fail(e, "uploading the mesh");
+  }
+  DevMesh &m = c->dm;
+  m.N = hm.N; m.p = hm.p; m.E = hm.E; m.ncol = hm.ncol; m.nslab = hm.nslab; m.n_layers = hm.n_layers;
+  m.bc_side = hm.bc_side; m.bc_bottom = hm.bc_bottom; m.penC = hm.penC;
+  m.colgeo = c->d_colgeo; m.slabgeo = c->d_slabgeo; m.colnb = c->d_colnb; m.colnbf = c->d_colnbf;
+  m.slab_layer = c->d_slab_layer; m.layer_c = nullptr;
+  c->ndof = (size_t)3 * hm.N * hm.N * hm.N * hm.E;
+  c->have_mesh = true;
+  return TN_OK;
+}
+
+tn_status tn_ndof(const tn_ctx *c, int64_t *ndof) {
+  if (!c || !ndof) return fail(TN_EINVAL, "null argument");
+  if (!c->have_mesh) return fail(TN_ESTATE, "no mesh");
+  *ndof = (int64_t)c->ndof;
+  return TN_OK;
+}
+
+tn_status tn_set_materials(tn_ctx *c, int n, const tn_material *mats) {
+  if (!c || !mats) return fail(TN_EINVAL, "null argument");
+  if (!c->have_mesh) return fail(TN_ESTATE, "no mesh: call tn_build_mesh first");
+  if (n != c->hm.n_layers) return fail(TN_EINVAL, "got %d materials for %d layers", n, c->hm.n_layers);
+  double *h = (double *)std::malloc(sizeof(double) * 3 * n);
+  if (!h) return fail(TN_ENOMEM, "host allocation failed");
+  for (int i = 0; i < n; ++i) {
+    const tn_material &m = mats[i];
+    double c11, c12, c44;
+    if (m.kind == TN_ISO) {
+      if (!(m.Y > 0.0) || !(m.nu > -1.0 && m.nu < 0.5)) {
+        std::free(h);
+        return fail(TN_EINVAL, "material %d: need Y > 0 and -1 < nu < 1/2", i);
+      }
+      const double mu = m.Y / (2.0 * (1.0 + m.nu));
+      const double lam = m.Y * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+      c11 = lam + 2.0 * mu; c12 = lam; c44 = mu;
+    } else if (m.kind == TN_CUBIC) {
+      // positive definiteness of the cubic stiffness
+      if (!(m.c44 > 0.0) || !(m.c11 > std::fabs(m.c12)) || !(m.c11 + 2.0 * m.c12 > 0.0)) {
+        std::free(h);
+        return fail(TN_EINVAL, "material %d: cubic stiffness not positive definite", i);
+      }
+      c11 = m.c11; c12 = m.c12; c44 = m.c44;
+    } else {
+      std::free(h);
+      return fail(TN_EINVAL, "material %d: unknown kind %d", i, m.kind);
+    }
+    h[3 * i] = c11; h[3 * i + 1] = c12; h[3 * i + 2] = c44;
+  }
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  CU_TRY(cudaStreamSynchronize(c->stream), "sync before replacing materials");
+  dfree(c->d_layer_c);
+  cudaError_t e = cudaMalloc((void **)&c->d_layer_c, sizeof(double) * 3 * n);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_layer_c, h, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  std::free(h);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading materials");
+  c->dm.layer_c = c->d_layer_c;
+  c->have_mat = true;
+  return TN_OK;
+}
+
+tn_status tn_set_beam(tn_ctx *c, double r0, double F0) {
+  if (!c) return fail(TN_EINVAL, "null context");
+  if (!(r0 > 0.0) || !std::isfinite(F0)) return fail(TN_EINVAL, "need r0 > 0 and finite F0");
+  c->r0 = r0;
+  c->F0 = F0;
+  c->have_beam = true;
+  return TN_OK;
+}
+
+static tn_status check_buf(const tn_ctx *c, const void *p, size_t elem, const char *name) {
+  if (!p) return fail(TN_EINVAL, "%s is null", name);
+  if (((uintptr_t)p) % 16) return fail(TN_EINVAL, "%s must be 16-byte aligned", name);
+  (void)c; (void)elem;
+  return TN_OK;
+}
+
+tn_status tn_apply_operator(tn_ctx *c, int precision, const void *u, void *y) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if (precision != TN_F64 && precision != TN_F32) return fail(TN_EINVAL, "precision must be TN_F64 or TN_F32");
+  const size_t es = precision == TN_F64 ? 8 : 4;
+  if ((st = check_buf(c, u, es, "u"))) return st;
+  if ((st = check_buf(c, y, es, "y"))) return st;
+  const char *a = (const char *)u, *b = (const char *)y;
+  const size_t bytes = c->ndof * es;
+  if (a < b + bytes && b < a + bytes) return fail(TN_EINVAL, "u and y overlap");
+  CU_TRY(tn_launch_apply(c->dm, precision, u, y, nullptr, nullptr, c->stream), "apply launch");
+  return TN_OK;
+}
+
+tn_status tn_rhs(tn_ctx *c, double *b) {
+  tn_status st = need_ready(c, true);
+  if (st) return st;
+  if ((st = check_buf(c, b, 8, "b"))) return st;
+  CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, b, c->stream), "rhs launch");
+  return TN_OK;
+}
+
+tn_status tn_diagonal(tn_ctx *c, double *d) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if ((st = check_buf(c, d, 8, "d"))) return st;
+  CU_TRY(tn_launch_diag(c->dm, d, c->stream), "diag launch");
+  return TN_OK;
+}
+
+tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report *rep) {
+  tn_status st = need_ready(c, true);
+  if (st) return st;
+  if (!o) return fail(TN_EINVAL, "opts is null");
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
+  if (o->precond != TN_PC_JACOBI) return fail(TN_EINVAL, "unknown preconditioner");
+  if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
+  if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
+  if (o->mode == TN_SOLVE_MIXED_F32 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0) || o->max_outer < 1))
+    return fail(TN_EINVAL, "mixed mode needs 0 < inner_rtol < 1 and max_outer >= 1");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  const int chunk = o->check_every > 0 ? o->check_every : 25;
+  const auto t0 = std::chrono::steady_clock::now();
+  tn::g_launches = 2;  // rhs and diagonal below
+  cudaStream_t s = c->sstream;
+  CU_TRY(cudaEventRecord(c->ev_in, c->stream), "event");
+  CU_TRY(cudaStreamWaitEvent(s, c->ev_in, 0), "event wait");
+  const size_t n = c->ndof;
+  CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, c->b64, s), "rhs");
+  CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
+  double bb = 0.0;
+  CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
+  tn_solve_report r{};
+  tn_status result = TN_OK;
+  if (bb == 0.0) {
+    CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
+  } else if (o->mode == TN_SOLVE_F64) {
+    CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv64, TN_F64, s), "dinv");
+    PcgVectors v{u, c->r64, c->z64, c->p64, c->q64, c->b64, c->dinv64};
+    int applies = 0;
+    CU_TRY(tn::pcg_f64(c->dm, n, v, o->use_x0 == 0, o->rtol, o->max_iter, chunk, c->scal, c->scal_host,
+                       c->part_elem, c->part_red, s, &applies), "pcg f64");
+    r.inner_iters = c->scal_host->iters;
+    r.outer_iters = 1;
+    r.applies_f64 = applies;
+    if (c->scal_host->breakdown) result = fail(TN_EBREAKDOWN, "CG breakdown after %d iterations", r.inner_iters);
+  } else {
+    CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
+    if (!o->use_x0) CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
+    int total_inner = 0;
+    for (int outer = 0; outer < o->max_outer; ++outer) {
+      double rr = 0.0;
+      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
+      r.applies_f64 += 1;
+      r.rel_residual = std::sqrt(rr / bb);
+      if (!std::isfinite(rr)) { result = fail(TN_EBREAKDOWN, "non-finite residual"); break; }
+      if (r.rel_residual <= o->rtol) break;
+      if (total_inner >= o->max_iter) break;
+      const double rn = std::sqrt(rr);
+      CU_TRY(tn::cast_scaled(n, c->r64, 1.0 / rn, c->b32, c->d32, s), "cast");
+      PcgVectors v{c->d32, c->r32, c->z32, c->p32, c->q32, c->b32, c->dinv32};
+      int applies = 0;
+      CU_TRY(tn::pcg_f32(c->dm, n, v, true, o->inner_rtol, o->max_iter - total_inner, chunk, c->scal,
+                         c->scal_host, c->part_elem, c->part_red, s, &applies), "pcg f32");
+      total_inner += c->scal_host->iters;
+      r.applies_f32 += applies;
+      r.outer_iters += 1;
+      if (c->scal_host->breakdown && c->scal_host->iters == 0) {
+        result = fail(TN_EBREAKDOWN, "inner CG breakdown");
+        break;
+      }
+      CU_TRY(tn::refine_update(n, u, c->d32, rn, s), "refine");
+    }
+    r.inner_iters = total_inner;
+  }
+  // true FP64 residual of the returned iterate
+  if (bb != 0.0 && result == TN_OK) {
+    double rr = 0.0;
+    CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
+    r.applies_f64 += 1;
+    r.rel_residual = std::sqrt(rr / bb);
+    if (!(r.rel_residual <= o->rtol))
+      result = fail(TN_ENOTCONV, "not converged: relative residual %.3e > %.3e after %d iterations",
+                    r.rel_residual, o->rtol, r.inner_iters);
+  }
+  CU_TRY(cudaEventRecord(c->ev_out, s), "event");
+  CU_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
+  CU_TRY(cudaStreamSynchronize(s), "sync");
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.status = result;
+  r.launches = tn::g_launches;
+  if (rep) *rep = r;
+  return result;
+}
+
+tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (!U_host) return fail(TN_EINVAL, "U_host is null");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  CU_TRY(tn_launch_energy(c->dm, u, c->elem_energy, c->layer_energy, c->stream), "energy launch");
+  CU_TRY(cudaMemcpyAsync(U_host, c->layer_energy, sizeof(double) * c->dm.n_layers, cudaMemcpyDeviceToHost,
+                         c->stream), "energy copy");
+  CU_TRY(cudaStreamSynchronize(c->stream), "energy sync");
+  return TN_OK;
+}
+
+tn_status tn_noise_psd(const double *U, const double *phi, int n, double kB_T, double f, double F0,
+                       double *S_out) {
+  if (!U || !phi || !S_out || n < 1) return fail(TN_EINVAL, "null argument or n < 1");
+  if (!(kB_T > 0.0) || !(f > 0.0) || !(F0 != 0.0)) return fail(TN_EINVAL, "need kB_T > 0, f > 0, F0 != 0");
+  double w = 0.0;
+  for (int i = 0; i < n; ++i) w += phi[i] * U[i];
+  *S_out = 4.0 * kB_T * w / (M_PI * f * F0 * F0);
+  return TN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,717 @@
+// sm_103a kernels of the DG elasticity operator (Sec. 2.2), its right-hand
+// side, diagonal and per-layer energies.
+//
+// Operator (weak form of Eq. (dg_residuals), LGL quadrature, M = w detJ):
+//   y = sum_m D_m^T F^m  -  sum_faces W ( 1/2 (T + T_ext) - sigma P[[u]] )
+//   F^m_j = J^-1[m][a] (Y : S_eff)^{aj},  S_eff = w detJ sym(grad u) + L,
+//   L = sum_faces W (-1/2) sym(n (x) [[u]])          (lifted auxiliary strain)
+// with W = w^S J^S at face nodes, T = n . Y grad u (unlifted, as in
+// Eq. (numfluxprimal)), [[u]] = u - u_ext, P[[u]] = n . Y_* : sym(n (x) [[u]])
+// (Eq. (constrel_avg)), sigma = C (p+1)^2 / min(h, h_ext) (Eq. (penalty)).
+// Dirichlet faces (Eq. (bc), u_b = 0): u_ext = -u, T_ext = T, Y_* = Y.
+// Neumann faces: no term.
+//
+// One CTA per element, one thread per node.  The element's own field is
+// staged in shared memory; for each interior face the neighbour's face values
+// and its logical normal derivative are gathered (neighbour data are L2
+// hits), then the neighbour traction is formed at the face nodes, then every
+// node forms its strain, stress, face terms and fluxes, and finally the
+// transposed derivative contractions give y.
+#include <cstdio>
+
+#include "tn_internal.h"
+
+__constant__ LglTables c_lgl;
+__constant__ float c_Df[TN_MAX_N + 1][TN_MAX_N * TN_MAX_N];
+__constant__ float c_wf[TN_MAX_N + 1][TN_MAX_N];
+
+cudaError_t tn_upload_lgl(const LglTables *t) {
+  cudaError_t err = cudaMemcpyToSymbol(c_lgl, t, sizeof(LglTables));
+  if (err != cudaSuccess) return err;
+  static float Df[TN_MAX_N + 1][TN_MAX_N * TN_MAX_N];
+  static float wf[TN_MAX_N + 1][TN_MAX_N];
+  for (int N = 0; N <= TN_MAX_N; ++N) {
+    for (int a = 0; a < TN_MAX_N * TN_MAX_N; ++a) Df[N][a] = (float)t->D[N][a];
+    for (int a = 0; a < TN_MAX_N; ++a) wf[N][a] = (float)t->w[N][a];
+  }
+  err = cudaMemcpyToSymbol(c_Df, Df, sizeof(Df));
+  if (err != cudaSuccess) return err;
+  return cudaMemcpyToSymbol(c_wf, wf, sizeof(wf));
+}
+
+namespace {
+
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double D(int N, int a, int b) { return c_lgl.D[N][a * N + b]; }
+  static __device__ __forceinline__ double w(int N, int a) { return c_lgl.w[N][a]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float D(int N, int a, int b) { return c_Df[N][a * N + b]; }
+  static __device__ __forceinline__ float w(int N, int a) { return c_wf[N][a]; }
+};
+
+// symmetric tensors as (xx, yy, zz, xy, xz, yz)
+template <typename T> struct Sym { T xx, yy, zz, xy, xz, yz; };
+
+// stress of a strain for a cubic-aligned stiffness (isotropic: c11 = l + 2m,
+// c12 = l, c44 = m): s_ii = (c11 - c12) S_ii + c12 tr S, s_ij = 2 c44 S_ij
+template <typename T>
+__device__ __forceinline__ Sym<T> stress(const Sym<T> &S, T c11, T c12, T c44) {
+  const T tr = S.xx + S.yy + S.zz, d = c11 - c12, two44 = c44 + c44;
+  return {d * S.xx + c12 * tr, d * S.yy + c12 * tr, d * S.zz + c12 * tr,
+          two44 * S.xy, two44 * S.xz, two44 * S.yz};
+}
+
+template <typename T>
+__device__ __forceinline__ void contract_n(const Sym<T> &s, const T n[3], T out[3]) {
+  out[0] = n[0] * s.xx + n[1] * s.xy + n[2] * s.xz;
+  out[1] = n[0] * s.xy + n[1] * s.yy + n[2] * s.yz;
+  out[2] = n[0] * s.xz + n[1] * s.yz + n[2] * s.zz;
+}
+
+template <typename T>
+__device__ __forceinline__ Sym<T> sym_outer(const T n[3], const T v[3]) {
+  const T h = T(0.5);
+  return {n[0] * v[0], n[1] * v[1], n[2] * v[2], h * (n[0] * v[1] + n[1] * v[0]),
+          h * (n[0] * v[2] + n[2] * v[0]), h * (n[1] * v[2] + n[2] * v[1])};
+}
+
+// physical gradient G[a][l] = sum_m Jinv[m][a] d_m u_l for the block-diagonal
+// J^-1 = [[ixx, ixy, 0], [iex, iey, 0], [0, 0, 1/dz]]; returns sym(G)
+template <typename T>
+__device__ __forceinline__ Sym<T> strain(const T dxi[3], const T deta[3], const T dzeta[3], T ixx,
+                                         T ixy, T iex, T iey, T idz) {
+  T G[3][3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    G[0][l] = ixx * dxi[l] + iex * deta[l];
+    G[1][l] = ixy * dxi[l] + iey * deta[l];
+    G[2][l] = idz * dzeta[l];
+  }
+  const T h = T(0.5);
+  return {G[0][0], G[1][1], G[2][2], h * (G[0][1] + G[1][0]), h * (G[0][2] + G[2][0]),
+          h * (G[1][2] + G[2][1])};
+}
+
+enum { FK_INTERIOR = 0, FK_DIRICHLET = 1, FK_NEUMANN = 2 };
+
+struct FaceInfo {
+  int kind[6];
+  int nb[6];      // neighbour element
+  int nbface[6];  // neighbour face 0..5
+  int flip[6];
+  int nbslab[6];
+  int nbcol[6];
+};
+
+// face kinds and neighbours of element (s, c)
+__device__ void face_info(const DevMesh &m, int s, int c, FaceInfo &fi, int f) {
+  if (f < 4) {
+    const int nbc = m.colnb[4 * c + f];
+    if (nbc >= 0) {
+      const int code = m.colnbf[4 * c + f];
+      fi.kind[f] = FK_INTERIOR;
+      fi.nb[f] = s * m.ncol + nbc;
+      fi.nbface[f] = code & 3;
+      fi.flip[f] = code >> 2;
+      fi.nbslab[f] = s;
+      fi.nbcol[f] = nbc;
+    } else {
+      fi.kind[f] = m.bc_side == TN_BC_FIXED ? FK_DIRICHLET : FK_NEUMANN;
+      fi.nb[f] = -1; fi.nbface[f] = 0; fi.flip[f] = 0; fi.nbslab[f] = s; fi.nbcol[f] = c;
+    }
+  } else if (f == 4) {  // zeta = -1: the slab below
+    if (s + 1 < m.nslab) {
+      fi.kind[f] = FK_INTERIOR; fi.nb[f] = (s + 1) * m.ncol + c; fi.nbface[f] = 5;
+      fi.flip[f] = 0; fi.nbslab[f] = s + 1; fi.nbcol[f] = c;
+    } else {
+      fi.kind[f] = m.bc_bottom == TN_BC_FIXED ? FK_DIRICHLET : FK_NEUMANN;
+      fi.nb[f] = -1; fi.nbface[f] = 0; fi.flip[f] = 0; fi.nbslab[f] = s; fi.nbcol[f] = c;
+    }
+  } else {  // zeta = +1: the slab above, or the top surface (beam, Neumann)
+    if (s > 0) {
+      fi.kind[f] = FK_INTERIOR; fi.nb[f] = (s - 1) * m.ncol + c; fi.nbface[f] = 4;
+      fi.flip[f] = 0; fi.nbslab[f] = s - 1; fi.nbcol[f] = c;
+    } else {
+      fi.kind[f] = FK_NEUMANN;
+      fi.nb[f] = -1; fi.nbface[f] = 0; fi.flip[f] = 0; fi.nbslab[f] = s; fi.nbcol[f] = c;
+    }
+  }
+}
+
+// node indices (i, j, k) of face node (t1, t2) on face f, end index set
+template <int N>
+__device__ __forceinline__ void face_node(int f, int t1, int t2, int &i, int &j, int &k) {
+  const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+  if (d == 0) { i = end; j = t1; k = t2; }
+  else if (d == 1) { i = t1; j = end; k = t2; }
+  else { i = t1; j = t2; k = end; }
+}
+
+// outward normal, W = w^S J^S and h = 2 detJ / J^S at a face node of face f,
+// from the column's 2x2 inverse map, its determinant and the slab's dz/dzeta;
+// wt is the product of the two tangential LGL weights of the node
+template <typename T>
+__device__ __forceinline__ void face_geom_w(int f, T wt, T ixx, T ixy, T iex, T iey, T det2, T dz,
+                                            T n[3], T &W, T &h) {
+  const int d = f >> 1;
+  const T sgn = (f & 1) ? T(1) : T(-1);
+  if (d == 2) {
+    n[0] = T(0); n[1] = T(0); n[2] = sgn;
+    W = wt * det2;
+    h = T(2) * dz;
+    return;
+  }
+  const T rx = d == 0 ? ixx : iex, ry = d == 0 ? ixy : iey;
+  const T mag = sqrt(rx * rx + ry * ry);
+  const T inv = T(1) / mag;
+  n[0] = sgn * rx * inv; n[1] = sgn * ry * inv; n[2] = T(0);
+  W = wt * det2 * dz * mag;
+  h = T(2) * inv;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void face_geom(int f, int i, int j, int k, T ixx, T ixy, T iex, T iey,
+                                          T det2, T dz, T n[3], T &W, T &h) {
+  const int d = f >> 1;
+  const T wt = d == 0 ? Tab<T>::w(N, j) * Tab<T>::w(N, k)
+                      : (d == 1 ? Tab<T>::w(N, i) * Tab<T>::w(N, k) : Tab<T>::w(N, i) * Tab<T>::w(N, j));
+  face_geom_w<T>(f, wt, ixx, ixy, iex, iey, det2, dz, n, W, h);
+}
+
+template <int N> __host__ __device__ constexpr int nthreads() { return ((N * N * N + 31) / 32) * 32; }
+
+template <int N, typename T>
+constexpr size_t apply_smem() {
+  return sizeof(T) * (12 * N * N * N + 42 * N * N);
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(nthreads<N>())
+apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *su = reinterpret_cast<T *>(smem_raw);  // [3][n]
+  T *sF = su + 3 * n;                        // [3][3][n]
+  T *nbv = sF + 9 * n;                       // [6][3][N2]
+  T *nbt = nbv + 18 * N2;                    // [6][3][N2] normal derivative, then traction
+  T *nbh = nbt + 18 * N2;                    // [6][N2]
+  __shared__ FaceInfo fi;
+  __shared__ T nbc[6][3];
+  __shared__ double red[NT / 32];
+
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  const T *ue = u + (size_t)e * 3 * n;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = ue[t];
+  if (tid < 6) {
+    face_info(m, s, c, fi, tid);
+    const int L = m.slab_layer[fi.nbslab[tid]];
+    nbc[tid][0] = (T)m.layer_c[3 * L + 0];
+    nbc[tid][1] = (T)m.layer_c[3 * L + 1];
+    nbc[tid][2] = (T)m.layer_c[3 * L + 2];
+  }
+  __syncthreads();
+
+  // ---- gather neighbour face values and logical normal derivatives
+  for (int t = tid; t < 6 * N2; t += NT) {
+    const int f = t / N2, q = t - f * N2;
+    if (fi.kind[f] != FK_INTERIOR) continue;
+    const int t1 = q % N, t2 = q / N;
+    const int f2 = fi.nbface[f], d2 = f2 >> 1, end = (f2 & 1) ? N - 1 : 0;
+    int i2, j2, k2;
+    if ((f >> 1) == 2) { i2 = t1; j2 = t2; k2 = end; }
+    else {
+      const int a = fi.flip[f] ? N - 1 - t1 : t1;
+      k2 = t2;
+      if (d2 == 0) { i2 = end; j2 = a; } else { i2 = a; j2 = end; }
+    }
+    const T *u2 = u + (size_t)fi.nb[f] * 3 * n;
+    const int stride = d2 == 0 ? 1 : (d2 == 1 ? N : N2);
+    const int base = (k2 * N + j2) * N + i2 - end * stride;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      T line[N];
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) line[mm] = u2[cc * n + base + mm * stride];
+      T dn = T(0);
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) dn += Tab<T>::D(N, end, mm) * line[mm];
+      nbv[(f * 3 + cc) * N2 + q] = line[end];
+      nbt[(f * 3 + cc) * N2 + q] = dn;
+    }
+    T h2;
+    if (d2 == 2) {
+      h2 = T(2) * (T)m.slabgeo[((size_t)fi.nbslab[f] * SG_NF + SG_DZ) * N + end];
+    } else {
+      const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
+      const int q2 = j2 * N + i2;
+      const T rx = (T)g2[(d2 == 0 ? CG_IXX : CG_IEX) * N2 + q2];
+      const T ry = (T)g2[(d2 == 0 ? CG_IXY : CG_IEY) * N2 + q2];
+      h2 = T(2) / sqrt(rx * rx + ry * ry);
+    }
+    nbh[f * N2 + q] = h2;
+  }
+  __syncthreads();
+
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
+  const int Lown = m.slab_layer[s];
+  const T c11 = (T)m.layer_c[3 * Lown], c12 = (T)m.layer_c[3 * Lown + 1], c44 = (T)m.layer_c[3 * Lown + 2];
+
+  // ---- neighbour traction n . Y_ext grad u_ext at the face nodes
+  for (int t = tid; t < 6 * N2; t += NT) {
+    const int f = t / N2, q = t - f * N2;
+    if (fi.kind[f] != FK_INTERIOR) continue;
+    const int t1 = q % N, t2 = q / N, d = f >> 1;
+    const int f2 = fi.nbface[f], d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+    T dt1[3], dt2[3], dn[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const T *v = nbv + (f * 3 + cc) * N2;
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a1 += Tab<T>::D(N, t1, mm) * v[t2 * N + mm];
+        a2 += Tab<T>::D(N, t2, mm) * v[mm * N + t1];
+      }
+      dt1[cc] = a1; dt2[cc] = a2;
+      dn[cc] = nbt[(f * 3 + cc) * N2 + q];
+    }
+    // neighbour logical derivatives in its own frame and its J^-1 there
+    T dxi[3], deta[3], dzeta[3];
+    T jxx, jxy, jex, jey, jdz;
+    int i, j, k;
+    face_node<N>(f, t1, t2, i, j, k);
+    if (d == 2) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) { dxi[cc] = dt1[cc]; deta[cc] = dt2[cc]; dzeta[cc] = dn[cc]; }
+      const int qq = j * N + i;
+      jxx = (T)cg[CG_IXX * N2 + qq]; jxy = (T)cg[CG_IXY * N2 + qq];
+      jex = (T)cg[CG_IEX * N2 + qq]; jey = (T)cg[CG_IEY * N2 + qq];
+      jdz = T(1) / (T)m.slabgeo[((size_t)fi.nbslab[f] * SG_NF + SG_DZ) * N + end2];
+    } else {
+      const T sg1 = fi.flip[f] ? T(-1) : T(1);
+      const int a = fi.flip[f] ? N - 1 - t1 : t1;
+      int i2, j2;
+      if (d2 == 0) {
+        i2 = end2; j2 = a;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) { dxi[cc] = dn[cc]; deta[cc] = sg1 * dt1[cc]; dzeta[cc] = dt2[cc]; }
+      } else {
+        i2 = a; j2 = end2;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) { deta[cc] = dn[cc]; dxi[cc] = sg1 * dt1[cc]; dzeta[cc] = dt2[cc]; }
+      }
+      const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
+      const int q2 = j2 * N + i2;
+      jxx = (T)g2[CG_IXX * N2 + q2]; jxy = (T)g2[CG_IXY * N2 + q2];
+      jex = (T)g2[CG_IEX * N2 + q2]; jey = (T)g2[CG_IEY * N2 + q2];
+      jdz = T(1) / (T)sg[SG_DZ * N + t2];
+    }
+    const Sym<T> S2 = strain(dxi, deta, dzeta, jxx, jxy, jex, jey, jdz);
+    const Sym<T> s2 = stress(S2, nbc[f][0], nbc[f][1], nbc[f][2]);
+    // our outward normal at this face node
+    const int qq = j * N + i;
+    T nrm[3], W, h;
+    face_geom<T, N>(f, i, j, k, (T)cg[CG_IXX * N2 + qq], (T)cg[CG_IXY * N2 + qq],
+                    (T)cg[CG_IEX * N2 + qq], (T)cg[CG_IEY * N2 + qq], (T)cg[CG_DET * N2 + qq],
+                    (T)sg[SG_DZ * N + k], nrm, W, h);
+    T tr[3];
+    contract_n(s2, nrm, tr);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) nbt[(f * 3 + cc) * N2 + q] = tr[cc];
+  }
+
+  // ---- per node: strain, stress, face terms, fluxes
+  T ysurf[3] = {T(0), T(0), T(0)};
+  const int p = tid;
+  const bool active = p < n;
+  const int i = p % N, j = (p / N) % N, k = p / N2;
+  if (active) {
+    T dxi[3], deta[3], dzeta[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const T *v = su + cc * n;
+      T a0 = T(0), a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a0 += Tab<T>::D(N, i, mm) * v[(k * N + j) * N + mm];
+        a1 += Tab<T>::D(N, j, mm) * v[(k * N + mm) * N + i];
+        a2 += Tab<T>::D(N, k, mm) * v[(mm * N + j) * N + i];
+      }
+      dxi[cc] = a0; deta[cc] = a1; dzeta[cc] = a2;
+    }
+    const int qq = j * N + i;
+    const T ixx = (T)cg[CG_IXX * N2 + qq], ixy = (T)cg[CG_IXY * N2 + qq];
+    const T iex = (T)cg[CG_IEX * N2 + qq], iey = (T)cg[CG_IEY * N2 + qq];
+    const T det2 = (T)cg[CG_DET * N2 + qq], dz = (T)sg[SG_DZ * N + k];
+    const T idz = T(1) / dz;
+    const Sym<T> S = strain(dxi, deta, dzeta, ixx, ixy, iex, iey, idz);
+    const T wJ = Tab<T>::w(N, i) * Tab<T>::w(N, j) * Tab<T>::w(N, k) * det2 * dz;
+    Sym<T> Se = {wJ * S.xx, wJ * S.yy, wJ * S.zz, wJ * S.xy, wJ * S.xz, wJ * S.yz};
+    const bool onface = i == 0 || i == N - 1 || j == 0 || j == N - 1 || k == 0 || k == N - 1;
+    if (onface) {
+      const Sym<T> sig = stress(S, c11, c12, c44);
+      const T sp1 = T((m.p + 1) * (m.p + 1)) * (T)m.penC;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int idx = d == 0 ? i : (d == 1 ? j : k);
+        if (idx != 0 && idx != N - 1) continue;
+        const int f = 2 * d + (idx == N - 1 ? 1 : 0);
+        const int kind = fi.kind[f];
+        if (kind == FK_NEUMANN) continue;
+        T nrm[3], W, h;
+        face_geom<T, N>(f, i, j, k, ixx, ixy, iex, iey, det2, dz, nrm, W, h);
+        T tr[3];
+        contract_n(sig, nrm, tr);
+        const int t1 = d == 0 ? j : i, t2 = d == 2 ? j : k;
+        const int q = t2 * N + t1;
+        const T uo[3] = {su[p], su[n + p], su[2 * n + p]};
+        T jump[3], tr2[3], h2, y11, y12, y44;
+        if (kind == FK_INTERIOR) {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            jump[cc] = uo[cc] - nbv[(f * 3 + cc) * N2 + q];
+            tr2[cc] = nbt[(f * 3 + cc) * N2 + q];
+          }
+          h2 = nbh[f * N2 + q];
+          y11 = T(0.5) * (c11 + nbc[f][0]);
+          y12 = T(0.5) * (c12 + nbc[f][1]);
+          y44 = T(0.5) * (c44 + nbc[f][2]);
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) { jump[cc] = uo[cc] + uo[cc]; tr2[cc] = tr[cc]; }
+          h2 = h; y11 = c11; y12 = c12; y44 = c44;
+        }
+        const T sigma = sp1 / (h < h2 ? h : h2);
+        const Sym<T> Ej = sym_outer(nrm, jump);
+        const Sym<T> Sj = stress(Ej, y11, y12, y44);
+        T pen[3];
+        contract_n(Sj, nrm, pen);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) ysurf[cc] -= W * (T(0.5) * (tr[cc] + tr2[cc]) - sigma * pen[cc]);
+        const T hw = T(-0.5) * W;
+        Se.xx += hw * Ej.xx; Se.yy += hw * Ej.yy; Se.zz += hw * Ej.zz;
+        Se.xy += hw * Ej.xy; Se.xz += hw * Ej.xz; Se.yz += hw * Ej.yz;
+      }
+    }
+    const Sym<T> se = stress(Se, c11, c12, c44);
+    // F^m_j = Jinv[m][a] sigma^{aj}
+    sF[(0 * 3 + 0) * n + p] = ixx * se.xx + ixy * se.xy;
+    sF[(0 * 3 + 1) * n + p] = ixx * se.xy + ixy * se.yy;
+    sF[(0 * 3 + 2) * n + p] = ixx * se.xz + ixy * se.yz;
+    sF[(1 * 3 + 0) * n + p] = iex * se.xx + iey * se.xy;
+    sF[(1 * 3 + 1) * n + p] = iex * se.xy + iey * se.yy;
+    sF[(1 * 3 + 2) * n + p] = iex * se.xz + iey * se.yz;
+    sF[(2 * 3 + 0) * n + p] = idz * se.xz;
+    sF[(2 * 3 + 1) * n + p] = idz * se.yz;
+    sF[(2 * 3 + 2) * n + p] = idz * se.zz;
+  }
+  __syncthreads();
+
+  // ---- weak divergence: y = sum_m D_m^T F^m
+  double dot = 0.0;
+  if (active) {
+    T *ye = y + (size_t)e * 3 * n;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const T *F0 = sF + (0 * 3 + cc) * n, *F1 = sF + (1 * 3 + cc) * n, *F2 = sF + (2 * 3 + cc) * n;
+      T acc = ysurf[cc];
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        acc += Tab<T>::D(N, mm, i) * F0[(k * N + j) * N + mm];
+        acc += Tab<T>::D(N, mm, j) * F1[(k * N + mm) * N + i];
+        acc += Tab<T>::D(N, mm, k) * F2[(mm * N + j) * N + i];
+      }
+      ye[cc * n + p] = acc;
+      dot += (double)acc * (double)su[cc * n + p];
+    }
+  }
+  if (partial) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if ((tid & 31) == 0) red[tid >> 5] = dot;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < NT / 32; ++w) sum += red[w];
+      partial[e] = sum;
+    }
+  }
+}
+
+template <int N, typename T>
+cudaError_t launch_apply_n(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+  constexpr size_t sm = apply_smem<N, T>();
+  static bool configured = false;  // per process; attribute is per function
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  apply_kernel<N, T><<<m.E, nthreads<N>(), sm, st>>>(m, u, y, partial);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply_t(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+  switch (m.N) {
+    case 3: return launch_apply_n<3, T>(m, u, y, partial, st);
+    case 4: return launch_apply_n<4, T>(m, u, y, partial, st);
+    case 5: return launch_apply_n<5, T>(m, u, y, partial, st);
+    case 6: return launch_apply_n<6, T>(m, u, y, partial, st);
+    case 7: return launch_apply_n<7, T>(m, u, y, partial, st);
+    case 8: return launch_apply_n<8, T>(m, u, y, partial, st);
+    case 9: return launch_apply_n<9, T>(m, u, y, partial, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- RHS
+// b = -sum_top W p(r) e_z at the top-surface nodes (Neumann beam data)
+__global__ void rhs_kernel(const DevMesh m, double r0, double F0, double *__restrict__ b) {
+  const int N = m.N, n = N * N * N, N2 = N * N;
+  const size_t total = (size_t)m.E * 3 * n;
+  const double norm = F0 / (M_PI * r0 * r0), ir2 = 1.0 / (r0 * r0);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(t % n);
+    const size_t ec = t / n;
+    const int cc = (int)(ec % 3);
+    const int e = (int)(ec / 3);
+    double v = 0.0;
+    if (cc == 2 && e < m.ncol && p / N2 == N - 1) {  // top slab, k = N-1, z component
+      const int q = p % N2, i = q % N, j = q / N;
+      const double *g = m.colgeo + (size_t)e * CG_NF * N2;
+      const double X = g[CG_X * N2 + q], Y = g[CG_Y * N2 + q];
+      const double W = c_lgl.w[N][i] * c_lgl.w[N][j] * g[CG_DET * N2 + q];
+      v = -W * norm * exp(-(X * X + Y * Y) * ir2);
+    }
+    b[t] = v;
+  }
+}
+
+// ------------------------------------------------------------ diagonal
+// diag(A) at (e, comp c, node p):
+//   volume: sum over the three lines through p of w detJ (c11 g_c^2 + c44 sum_{a!=c} g_a^2)
+//           with g the physical gradient of the basis function at the node
+//   face f containing p (non-Neumann): -2 W Q + 2 W sigma (c11* n_c^2 + c44* (1 - n_c^2)) x s
+//           with Q = c11 n_c g_c + c44 sum_{a != c} n_a g_a, interior: factor 1/2 on both.
+__global__ void diag_kernel(const DevMesh m, double *__restrict__ dg) {
+  const int N = m.N, n = N * N * N, N2 = N * N;
+  const int e = blockIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  __shared__ FaceInfo fi;
+  __shared__ double nbc[6][3];
+  if (threadIdx.x < 6) {
+    face_info(m, s, c, fi, threadIdx.x);
+    const int L = m.slab_layer[fi.nbslab[threadIdx.x]];
+    for (int a = 0; a < 3; ++a) nbc[threadIdx.x][a] = m.layer_c[3 * L + a];
+  }
+  __syncthreads();
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
+  const int L = m.slab_layer[s];
+  const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
+  (void)c12;
+#define DD(a, b) c_lgl.D[N][(a) * N + (b)]
+#define WW(a) c_lgl.w[N][(a)]
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int i = p % N, j = (p / N) % N, k = p / N2;
+    double out[3] = {0.0, 0.0, 0.0};
+    // volume: nodes r on the three lines through p
+    for (int line = 0; line < 3; ++line) {
+      for (int r = 0; r < N; ++r) {
+        int ri = i, rj = j, rk = k;
+        if (line == 0) ri = r; else if (line == 1) rj = r; else rk = r;
+        const bool self = (ri == i && rj == j && rk == k);
+        if (self && line > 0) continue;  // count r = p once
+        const int q = rj * N + ri;
+        double lg[3];
+        if (self) { lg[0] = DD(i, i); lg[1] = DD(j, j); lg[2] = DD(k, k); }
+        else {
+          lg[0] = line == 0 ? DD(ri, i) : 0.0;
+          lg[1] = line == 1 ? DD(rj, j) : 0.0;
+          lg[2] = line == 2 ? DD(rk, k) : 0.0;
+        }
+        const double ixx = cg[CG_IXX * N2 + q], ixy = cg[CG_IXY * N2 + q];
+        const double iex = cg[CG_IEX * N2 + q], iey = cg[CG_IEY * N2 + q];
+        const double dz = sg[SG_DZ * N + rk];
+        const double g[3] = {ixx * lg[0] + iex * lg[1], ixy * lg[0] + iey * lg[1], lg[2] / dz};
+        const double wJ = WW(ri) * WW(rj) * WW(rk) * cg[CG_DET * N2 + q] * dz;
+        const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        for (int cc = 0; cc < 3; ++cc) out[cc] += wJ * (c11 * g[cc] * g[cc] + c44 * (g2 - g[cc] * g[cc]));
+      }
+    }
+    // faces
+    const int q = j * N + i;
+    const double ixx = cg[CG_IXX * N2 + q], ixy = cg[CG_IXY * N2 + q];
+    const double iex = cg[CG_IEX * N2 + q], iey = cg[CG_IEY * N2 + q];
+    const double det2 = cg[CG_DET * N2 + q], dz = sg[SG_DZ * N + k];
+    const double lg[3] = {DD(i, i), DD(j, j), DD(k, k)};
+    const double g[3] = {ixx * lg[0] + iex * lg[1], ixy * lg[0] + iey * lg[1], lg[2] / dz};
+    const double sp1 = (double)((m.p + 1) * (m.p + 1)) * m.penC;
+    for (int d = 0; d < 3; ++d) {
+      const int idx = d == 0 ? i : (d == 1 ? j : k);
+      if (idx != 0 && idx != N - 1) continue;
+      const int f = 2 * d + (idx == N - 1 ? 1 : 0);
+      if (fi.kind[f] == FK_NEUMANN) continue;
+      double nrm[3], W, h;
+      const double wt = d == 0 ? WW(j) * WW(k) : (d == 1 ? WW(i) * WW(k) : WW(i) * WW(j));
+      face_geom_w<double>(f, wt, ixx, ixy, iex, iey, det2, dz, nrm, W, h);
+      double h2, y11, y44, fac;
+      if (fi.kind[f] == FK_INTERIOR) {
+        // neighbour h at the matching node
+        const int t1 = d == 0 ? j : i, t2 = d == 2 ? j : k;
+        const int f2 = fi.nbface[f], d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+        if (d == 2) {
+          h2 = 2.0 * m.slabgeo[((size_t)fi.nbslab[f] * SG_NF + SG_DZ) * N + end2];
+        } else {
+          const int a = fi.flip[f] ? N - 1 - t1 : t1;
+          const int i2 = d2 == 0 ? end2 : a, j2 = d2 == 0 ? a : end2;
+          const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
+          const double rx = g2[(d2 == 0 ? CG_IXX : CG_IEX) * N2 + j2 * N + i2];
+          const double ry = g2[(d2 == 0 ? CG_IXY : CG_IEY) * N2 + j2 * N + i2];
+          h2 = 2.0 / sqrt(rx * rx + ry * ry);
+        }
+        (void)t2;
+        y11 = 0.5 * (c11 + nbc[f][0]);
+        y44 = 0.5 * (c44 + nbc[f][2]);
+        fac = 0.5;
+      } else {
+        h2 = h; y11 = c11; y44 = c44; fac = 1.0;
+      }
+      const double sigma = sp1 / (h < h2 ? h : h2);
+      for (int cc = 0; cc < 3; ++cc) {
+        double Qc = 0.0;
+        for (int a = 0; a < 3; ++a) Qc += (a == cc ? c11 : c44) * nrm[a] * g[a];
+        const double pn = y11 * nrm[cc] * nrm[cc] + y44 * (1.0 - nrm[cc] * nrm[cc]);
+        out[cc] += -2.0 * fac * W * Qc + (fac == 0.5 ? 1.0 : 2.0) * W * sigma * pn;
+      }
+    }
+    for (int cc = 0; cc < 3; ++cc) dg[((size_t)e * 3 + cc) * n + p] = out[cc];
+  }
+#undef DD
+#undef WW
+}
+
+// ------------------------------------------------------------- energies
+// elem[e] = 1/2 sum_p w_p detJ_p S_p : Y : S_p, S = sym grad u (unlifted)
+template <int N>
+__global__ void __launch_bounds__(nthreads<N>())
+energy_kernel(const DevMesh m, const double *__restrict__ u, double *__restrict__ elem) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  __shared__ double su[3 * n];
+  __shared__ double red[NT / 32];
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = u[(size_t)e * 3 * n + t];
+  __syncthreads();
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
+  const int L = m.slab_layer[s];
+  const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
+  double en = 0.0;
+  if (tid < n) {
+    const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
+    double dxi[3], deta[3], dzeta[3];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double *v = su + cc * n;
+      double a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a0 += Tab<double>::D(N, i, mm) * v[(k * N + j) * N + mm];
+        a1 += Tab<double>::D(N, j, mm) * v[(k * N + mm) * N + i];
+        a2 += Tab<double>::D(N, k, mm) * v[(mm * N + j) * N + i];
+      }
+      dxi[cc] = a0; deta[cc] = a1; dzeta[cc] = a2;
+    }
+    const int q = j * N + i;
+    const double dz = sg[SG_DZ * N + k];
+    const Sym<double> S = strain(dxi, deta, dzeta, cg[CG_IXX * N2 + q], cg[CG_IXY * N2 + q],
+                                 cg[CG_IEX * N2 + q], cg[CG_IEY * N2 + q], 1.0 / dz);
+    const Sym<double> sg2 = stress(S, c11, c12, c44);
+    const double dens = S.xx * sg2.xx + S.yy * sg2.yy + S.zz * sg2.zz +
+                        2.0 * (S.xy * sg2.xy + S.xz * sg2.xz + S.yz * sg2.yz);
+    en = 0.5 * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) *
+         cg[CG_DET * N2 + q] * dz * dens;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
+  if ((tid & 31) == 0) red[tid >> 5] = en;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    elem[e] = sum;
+  }
+}
+
+// one block: per layer, sum the element energies slab by slab in a fixed order
+__global__ void layer_sum_kernel(const DevMesh m, const double *__restrict__ elem, double *__restrict__ out) {
+  __shared__ double red[32];
+  for (int L = 0; L < m.n_layers; ++L) {
+    double acc = 0.0;
+    for (int s = 0; s < m.nslab; ++s) {
+      if (m.slab_layer[s] != L) continue;
+      for (int c = threadIdx.x; c < m.ncol; c += blockDim.x) acc += elem[(size_t)s * m.ncol + c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+      out[L] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+template <int N>
+cudaError_t launch_energy_n(const DevMesh &m, const double *u, double *elem, cudaStream_t st) {
+  energy_kernel<N><<<m.E, nthreads<N>(), 0, st>>>(m, u, elem);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
+                            double *partial, const void *dotwith, cudaStream_t st) {
+  (void)dotwith;
+  if (precision == TN_F64)
+    return launch_apply_t<double>(m, (const double *)u, (double *)y, partial, st);
+  return launch_apply_t<float>(m, (const float *)u, (float *)y, partial, st);
+}
+
+cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st) {
+  rhs_kernel<<<4 * 152, 256, 0, st>>>(m, r0, F0, b);
+  return cudaGetLastError();
+}
+
+cudaError_t tn_launch_diag(const DevMesh &m, double *d, cudaStream_t st) {
+  diag_kernel<<<m.E, 128, 0, st>>>(m, d);
+  return cudaGetLastError();
+}
+
+cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem, double *layer,
+                             cudaStream_t st) {
+  cudaError_t err;
+  switch (m.N) {
+    case 3: err = launch_energy_n<3>(m, u, elem, st); break;
+    case 4: err = launch_energy_n<4>(m, u, elem, st); break;
+    case 5: err = launch_energy_n<5>(m, u, elem, st); break;
+    case 6: err = launch_energy_n<6>(m, u, elem, st); break;
+    case 7: err = launch_energy_n<7>(m, u, elem, st); break;
+    case 8: err = launch_energy_n<8>(m, u, elem, st); break;
+    case 9: err = launch_energy_n<9>(m, u, elem, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (err != cudaSuccess) return err;
+  layer_sum_kernel<<<1, 256, 0, st>>>(m, elem, layer);
+  return cudaGetLastError();
+}

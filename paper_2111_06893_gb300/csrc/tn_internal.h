@@ -1,0 +1,80 @@
+// Internal structures shared by the host code and the kernels of the
+// thermonoise library.  Geometry is stored factorised: every element map of
+// the box and cylinder meshes is x(xi, eta, zeta) = (X(xi, eta), Y(xi, eta),
+// Z(zeta)) -- a cross-section map of the element's column times a vertical
+// map of its slab -- so the Jacobian is block diagonal and the per-node
+// geometry of Sec. 2.2.1 (J, det J, J^-1) is the product of a 2-D column
+// table and a 1-D slab table.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/thermonoise.h"
+
+#define TN_MAX_N 9
+#define TN_MIN_N 3
+
+// column geometry, per column and per cross-section node q = j * N + i
+enum {
+  CG_IXX = 0,  // dxi/dx
+  CG_IXY = 1,  // dxi/dy
+  CG_IEX = 2,  // deta/dx
+  CG_IEY = 3,  // deta/dy
+  CG_DET = 4,  // det of d(X, Y)/d(xi, eta)
+  CG_X = 5,    // X
+  CG_Y = 6,    // Y
+  CG_NF = 7
+};
+// slab geometry, per slab and per node k along zeta
+enum { SG_DZ = 0, SG_Z = 1, SG_NF = 2 };
+
+struct DevMesh {
+  int N;          // LGL points per dimension
+  int p;          // degree
+  int E;          // elements
+  int ncol;       // columns
+  int nslab;      // slabs
+  int n_layers;
+  int bc_side;    // TN_BC_*
+  int bc_bottom;
+  double penC;    // penalty constant C
+  const double *colgeo;   // [ncol][CG_NF][N*N]
+  const double *slabgeo;  // [nslab][SG_NF][N]
+  const int *colnb;       // [ncol][4]: neighbour column across faces xi-, xi+, eta-, eta+ (-1: side)
+  const int *colnbf;      // [ncol][4]: neighbour face (0..3) | (flip << 2)
+  const int *slab_layer;  // [nslab]
+  const double *layer_c;  // [n_layers][3]: c11, c12, c44 (isotropic: lambda+2mu, lambda, mu)
+};
+
+// LGL tables in constant memory, indexed by N (filled at context creation)
+struct LglTables {
+  double x[TN_MAX_N + 1][TN_MAX_N];
+  double w[TN_MAX_N + 1][TN_MAX_N];
+  double D[TN_MAX_N + 1][TN_MAX_N * TN_MAX_N];  // D[a*N+b] = l_b'(x_a)
+};
+
+// host-side helpers (mesh.cpp)
+namespace tn {
+void lgl(int N, double *x, double *w, double *D);
+struct HostMesh {
+  int N = 0, p = 0, E = 0, ncol = 0, nslab = 0, n_layers = 0;
+  int bc_side = 0, bc_bottom = 0;
+  double penC = 0;
+  double *colgeo = nullptr;
+  double *slabgeo = nullptr;
+  int *colnb = nullptr, *colnbf = nullptr, *slab_layer = nullptr;
+};
+// fills host arrays (malloc'ed) from a description; returns TN_OK or TN_EINVAL with msg
+tn_status build_host_mesh(const tn_mesh_desc *d, HostMesh *out, char *msg, int msglen);
+void free_host_mesh(HostMesh *m);
+}  // namespace tn
+
+// kernels (kernels.cu) -- launchers return cudaError_t of the launch
+cudaError_t tn_upload_lgl(const LglTables *t);
+cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
+                            double *partial, const void *dotwith, cudaStream_t st);
+cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st);
+cudaError_t tn_launch_diag(const DevMesh &m, double *d, cudaStream_t st);
+cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem_energy,
+                             double *layer_energy, cudaStream_t st);

@@ -1,0 +1,40 @@
+// Krylov solver internals (solver.cu) used by the C ABI layer.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+// device-resident Krylov scalars of one PCG run
+struct tn_pcg_scalars {
+  double rz, rr, rr0, pq, alpha, beta, tol2;
+  int iters, max_iters, done, breakdown;
+};
+
+// vectors of one PCG run, all of the run's precision
+struct PcgVectors {
+  void *x, *r, *z, *p, *q;
+  const void *b, *dinv;
+};
+
+namespace tn {
+// kernel launches issued on behalf of the current solve (host counter)
+extern thread_local long long g_launches;
+cudaError_t pcg_setup_dinv(const DevMesh &m, size_t n, const double *diag, void *dinv, int prec,
+                           cudaStream_t st);
+cudaError_t pcg_f64(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+                    int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
+                    double *part_red, cudaStream_t st, int *applies);
+cudaError_t pcg_f32(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+                    int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
+                    double *part_red, cudaStream_t st, int *applies);
+cudaError_t residual_f64(const DevMesh &m, size_t n, const double *b, const double *x, double *Ax, double *r,
+                         double *part_red, double *sum_dev, double *rr_host, cudaStream_t st);
+cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_dev, double *out_host,
+                      cudaStream_t st);
+cudaError_t cast_scaled(size_t n, const double *r64, double scale, float *r32, float *d32, cudaStream_t st);
+cudaError_t refine_update(size_t n, double *x, const float *d, double scale, cudaStream_t st);
+cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st);
+int reduction_blocks();
+}  // namespace tn

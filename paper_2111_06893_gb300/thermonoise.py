@@ -1,0 +1,277 @@
+"""Python binding of the thermonoise C ABI (include/thermonoise.h).
+
+Argument marshalling only: every step runs in the CUDA library.  PyTorch
+supplies device memory (tensors) and the CUDA stream.  There is no CPU
+fallback: if the shared library is missing or no GPU is present the calls
+raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libthermonoise.so")
+
+TN_OK = 0
+TN_EINVAL_CODE = -1
+TN_MESH_BOX, TN_MESH_CYLINDER = 0, 1
+TN_BC_FREE, TN_BC_FIXED = 0, 1
+TN_F64, TN_F32 = 0, 1
+TN_ISO, TN_CUBIC = 0, 1
+TN_SOLVE_F64, TN_SOLVE_MIXED_F32 = 0, 1
+TN_PC_JACOBI = 0
+STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_ENOTCONV",
+          -5: "TN_EBREAKDOWN", -6: "TN_ETIMEOUT", -7: "TN_ESTATE"}
+
+# every entry point declared in include/thermonoise.h
+SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
+           "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
+           "tn_solve", "tn_layer_energies", "tn_noise_psd"]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("degree", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("x_breaks", C.POINTER(C.c_double)), ("y_breaks", C.POINTER(C.c_double)),
+                ("R", C.c_double), ("a", C.c_double), ("R1", C.c_double), ("k", C.c_int),
+                ("n_slabs", C.c_int), ("slab_z", C.POINTER(C.c_double)),
+                ("slab_layer", C.POINTER(C.c_int)), ("slab_log", C.POINTER(C.c_int)),
+                ("n_layers", C.c_int), ("penalty_C", C.c_double), ("bc_side", C.c_int),
+                ("bc_bottom", C.c_int)]
+
+
+class Material(C.Structure):
+    _fields_ = [("kind", C.c_int), ("Y", C.c_double), ("nu", C.c_double),
+                ("c11", C.c_double), ("c12", C.c_double), ("c44", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
+                ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
+                ("use_x0", C.c_int), ("check_every", C.c_int)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
+                ("applies_f64", C.c_int), ("applies_f32", C.c_int), ("launches", C.c_int64),
+                ("rel_residual", C.c_double),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ThermonoiseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libthermonoise.so (fails loudly if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2111_06893_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    sig = {
+        "tn_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+        "tn_destroy": (None, [vp]),
+        "tn_last_error": (C.c_char_p, []),
+        "tn_build_mesh": (C.c_int, [vp, C.POINTER(MeshDesc)]),
+        "tn_ndof": (C.c_int, [vp, i64p]),
+        "tn_set_materials": (C.c_int, [vp, C.c_int, C.POINTER(Material)]),
+        "tn_set_beam": (C.c_int, [vp, C.c_double, C.c_double]),
+        "tn_apply_operator": (C.c_int, [vp, C.c_int, vp, vp]),
+        "tn_rhs": (C.c_int, [vp, vp]),
+        "tn_diagonal": (C.c_int, [vp, vp]),
+        "tn_solve": (C.c_int, [vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
+        "tn_layer_energies": (C.c_int, [vp, vp, dp]),
+        "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != TN_OK:
+        raise ThermonoiseError(status, load().tn_last_error().decode())
+
+
+def _dptr(arr, ctype):
+    arr = np.ascontiguousarray(arr, dtype=np.float64 if ctype is C.c_double else np.int32)
+    return arr, arr.ctypes.data_as(C.POINTER(ctype))
+
+
+def mesh_struct(desc):
+    """tn_mesh_desc from a workload description (keeps the arrays alive)."""
+    keep = []
+    d = MeshDesc()
+    d.kind = TN_MESH_BOX if desc["kind"] == "box" else TN_MESH_CYLINDER
+    d.degree = int(desc["degree"])
+    if desc["kind"] == "box":
+        xb, px = _dptr(desc["x_breaks"], C.c_double)
+        yb, py = _dptr(desc["y_breaks"], C.c_double)
+        keep += [xb, yb]
+        d.nx, d.ny, d.x_breaks, d.y_breaks = len(xb) - 1, len(yb) - 1, px, py
+    else:
+        d.R, d.a, d.R1, d.k = desc["R"], desc["a"], desc["R1"], int(desc["k"])
+    sz, pz = _dptr(desc["slab_z"], C.c_double)
+    sl, pl = _dptr(desc["slab_layer"], C.c_int)
+    lg, pg = _dptr(desc["slab_log"], C.c_int)
+    keep += [sz, sl, lg]
+    d.n_slabs, d.slab_z, d.slab_layer, d.slab_log = len(sz) - 1, pz, pl, pg
+    d.n_layers = len(desc["materials"])
+    d.penalty_C = float(desc["penalty_C"])
+    d.bc_side = TN_BC_FIXED if desc["bc_side"] == "fixed" else TN_BC_FREE
+    d.bc_bottom = TN_BC_FIXED if desc["bc_bottom"] == "fixed" else TN_BC_FREE
+    return d, keep
+
+
+def material_array(mats):
+    arr = (Material * len(mats))()
+    for i, m in enumerate(mats):
+        if m["kind"] == "iso":
+            arr[i].kind, arr[i].Y, arr[i].nu = TN_ISO, m["Y"], m["nu"]
+        else:
+            arr[i].kind = TN_CUBIC
+            arr[i].c11, arr[i].c12, arr[i].c44 = m["c11"], m["c12"], m["c44"]
+    return arr
+
+
+class Context:
+    """One tn_ctx on a CUDA device; work goes on torch's current stream of
+    that device unless a stream is given."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("thermonoise needs a CUDA GPU; there is no CPU path")
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        _check(lib.tn_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self.desc = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- set-up
+    def build_mesh(self, desc):
+        d, keep = mesh_struct(desc)
+        _check(load().tn_build_mesh(self._h, C.byref(d)))
+        del keep
+        self.desc = desc
+        return self
+
+    def set_materials(self, mats):
+        arr = material_array(mats)
+        _check(load().tn_set_materials(self._h, len(mats), arr))
+        return self
+
+    def set_beam(self, r0, F0):
+        _check(load().tn_set_beam(self._h, float(r0), float(F0)))
+        return self
+
+    @property
+    def ndof(self):
+        n = C.c_int64()
+        _check(load().tn_ndof(self._h, C.byref(n)))
+        return n.value
+
+    def _vec(self, dtype):
+        return self._torch.empty(self.ndof, dtype=dtype, device=self.device)
+
+    def _check_tensor(self, t, dtype, name):
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() == self.ndof):
+            raise ValueError(f"{name}: need a contiguous {dtype} CUDA tensor of {self.ndof} values")
+
+    # ---- operator and data
+    def apply_operator(self, u, y=None):
+        torch = self._torch
+        prec = TN_F64 if u.dtype == torch.float64 else TN_F32
+        if y is None:
+            y = torch.empty_like(u)
+        self._check_tensor(u, u.dtype, "u")
+        self._check_tensor(y, u.dtype, "y")
+        _check(load().tn_apply_operator(self._h, prec, C.c_void_p(u.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def rhs(self, out=None):
+        out = self._vec(self._torch.float64) if out is None else out
+        self._check_tensor(out, self._torch.float64, "b")
+        _check(load().tn_rhs(self._h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def diagonal(self, out=None):
+        out = self._vec(self._torch.float64) if out is None else out
+        self._check_tensor(out, self._torch.float64, "d")
+        _check(load().tn_diagonal(self._h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-5, max_iter=200000, max_outer=50,
+              x0=None, check_every=25, out=None, raise_on_error=True):
+        o = SolveOpts()
+        o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
+        o.precond = TN_PC_JACOBI
+        o.rtol, o.inner_rtol = rtol, inner_rtol
+        o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
+        u = out if out is not None else self._vec(self._torch.float64)
+        o.use_x0 = 0
+        if x0 is not None:
+            u.copy_(x0)
+            o.use_x0 = 1
+        rep = SolveReport()
+        st = load().tn_solve(self._h, C.byref(o), C.c_void_p(u.data_ptr()), C.byref(rep))
+        if raise_on_error:
+            _check(st)
+        return u, rep.as_dict()
+
+    def layer_energies(self, u):
+        self._check_tensor(u, self._torch.float64, "u")
+        n = len(self.desc["materials"])
+        U = np.zeros(n)
+        _check(load().tn_layer_energies(self._h, C.c_void_p(u.data_ptr()),
+                                        U.ctypes.data_as(C.POINTER(C.c_double))))
+        return U
+
+
+def noise_psd(U, phi, kB_T, f, F0):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    if U.shape != phi.shape:
+        raise ValueError("U and phi need the same length")
+    out = C.c_double()
+    _check(load().tn_noise_psd(U.ctypes.data_as(C.POINTER(C.c_double)),
+                               phi.ctypes.data_as(C.POINTER(C.c_double)), len(U), kB_T, f, F0,
+                               C.byref(out)))
+    return out.value
+
+
+def setup(desc, device=0, stream=None):
+    """Context with mesh, materials and beam of a workload description."""
+    ctx = Context(device, stream)
+    ctx.build_mesh(desc)
+    ctx.set_materials(desc["materials"])
+    ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
+    return ctx

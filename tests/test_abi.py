@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every declared entry point
+(no GPU needed); host-only entry points and argument checks run on CPU."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_06893_gb300 import build, thermonoise
+    build.build()
+    return thermonoise.load()
+
+
+def declared_symbols():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            src = open(os.path.join(inc, fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(tn_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2111_06893_gb300 import thermonoise
+    names = declared_symbols()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(thermonoise.SYMBOLS) <= set(names)
+
+
+def test_noise_psd_host_entry_point(lib):
+    from oracle import observables as ob
+    from paper_2111_06893_gb300 import thermonoise
+    U = np.array([1.5e-13, 2.0e-12])
+    phi = np.array([4e-4, 1e-6])
+    kT = 300 * ob.BOLTZMANN
+    S = thermonoise.noise_psd(U, phi, kT, 100.0, 2.0)
+    assert math.isclose(S, ob.noise_psd(U, phi, kT, 100.0, 2.0), rel_tol=1e-15)
+    with pytest.raises(thermonoise.ThermonoiseError):
+        thermonoise.noise_psd(U, phi, -1.0, 100.0, 2.0)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    st = lib.tn_create(C.byref(h), 0, None)
+    assert st != 0 and not h.value
+    assert len(lib.tn_last_error()) > 0
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.tn_build_mesh(None, None) == -1
+    assert lib.tn_apply_operator(None, 0, None, None) == -1
+    assert lib.tn_solve(None, None, None, None) == -1
+    lib.tn_destroy(None)

@@ -1,0 +1,177 @@
+"""Parity of the CUDA path with the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 operator applies 1e-11 relative to max|y| (element by
+element), energies 1e-9 relative; FP32 applies 2e-5 relative to max|y|
+(single rounding of the fields and geometry plus FP32 accumulation over
+~10^2 terms per output).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Mesh, Operator, observables as ob
+
+from cases import CASES
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_06893_gb300 import build
+    build.build()
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(name):
+    desc = CASES[name]()
+    op = Operator(Mesh(desc))
+    A = op.assemble()
+    return desc, op, A
+
+
+def gpu_ctx(desc):
+    from paper_2111_06893_gb300 import thermonoise
+    return thermonoise.setup(desc)
+
+
+def to_dev(x, dtype=torch.float64):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_apply_f64_matches_oracle(name):
+    desc, op, A = oracle_case(name)
+    ctx = gpu_ctx(desc)
+    assert ctx.ndof == op.mesh.ndof
+    for seed in (0, 1):
+        u = W.random_field(desc, seed)
+        y = ctx.apply_operator(to_dev(u)).cpu().numpy()
+        yo = A @ u
+        err = np.max(np.abs(y - yo)) / np.max(np.abs(yo))
+        assert err < 1e-11, (name, seed, err)
+
+
+@pytest.mark.parametrize("name", ["plain_box", "box_layers_p4", "cyl_small_p4_k2", "cyl_thin_p5"])
+def test_apply_f32_matches_oracle(name):
+    desc, op, A = oracle_case(name)
+    ctx = gpu_ctx(desc)
+    u = W.random_field(desc, 3)
+    u32 = u.astype(np.float32)
+    y = ctx.apply_operator(to_dev(u32, torch.float32)).cpu().numpy().astype(np.float64)
+    yo = A @ u32.astype(np.float64)
+    err = np.max(np.abs(y - yo)) / np.max(np.abs(yo))
+    assert err < 2e-5, (name, err)
+
+
+@pytest.mark.parametrize("name", ["plain_box", "box_layers_p4", "cyl_small_p4_k2", "cyl_small_p7_k1_fixed"])
+def test_rhs_and_diagonal_match_oracle(name):
+    desc, op, A = oracle_case(name)
+    ctx = gpu_ctx(desc)
+    b = ctx.rhs().cpu().numpy()
+    bo = op.rhs()
+    assert np.max(np.abs(b - bo)) <= 1e-14 * np.max(np.abs(bo))
+    d = ctx.diagonal().cpu().numpy()
+    do = A.diagonal()
+    assert np.max(np.abs(d - do) / np.abs(do)) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["box_layers_p4", "cyl_small_p4_k2", "cyl_thin_p5"])
+def test_energies_match_oracle_on_random_field(name):
+    desc, op, A = oracle_case(name)
+    ctx = gpu_ctx(desc)
+    u = W.random_field(desc, 5)
+    U = ctx.layer_energies(to_dev(u))
+    Uo = ob.layer_energies(op, u)
+    assert np.max(np.abs(U - Uo) / np.abs(Uo)) < 1e-12
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_solve_plain_box_energies_match_oracle_direct_solve(mode):
+    desc, op, A = oracle_case("plain_box")
+    uo = ob.solve_dense(A, op.rhs())
+    Uo = ob.layer_energies(op, uo)
+    ctx = gpu_ctx(desc)
+    u, rep = ctx.solve(mode=mode, rtol=1e-13)
+    assert rep["rel_residual"] <= 1e-13
+    U = ctx.layer_energies(u)
+    assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (U, Uo)
+    un = u.cpu().numpy()
+    assert np.max(np.abs(un - uo)) < 1e-9 * np.max(np.abs(uo))
+    if mode == "mixed":
+        assert rep["applies_f32"] > rep["applies_f64"]
+
+
+def test_solve_layered_cylinder_matches_oracle():
+    desc, op, A = oracle_case("cyl_small_p4_k1")
+    uo = ob.solve_dense(A, op.rhs())
+    Uo = ob.layer_energies(op, uo)
+    ctx = gpu_ctx(desc)
+    for mode in ("f64", "mixed"):
+        u, rep = ctx.solve(mode=mode, rtol=1e-13)
+        U = ctx.layer_energies(u)
+        assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (mode, U, Uo)
+    from paper_2111_06893_gb300 import noise_psd
+    phi = [1e-4, 4e-4, 1e-6]
+    S = noise_psd(U, phi, 4.14e-21, 100.0, desc["beam"]["F0"])
+    So = ob.noise_psd(Uo, phi, 4.14e-21, 100.0, desc["beam"]["F0"])
+    assert abs(S / So - 1) < 1e-9
+
+
+def test_apply_is_deterministic():
+    desc, op, A = oracle_case("cyl_small_p4_k2")
+    ctx = gpu_ctx(desc)
+    u = to_dev(W.random_field(desc, 9))
+    y1 = ctx.apply_operator(u).clone()
+    y2 = ctx.apply_operator(u)
+    assert torch.equal(y1, y2)
+
+
+def test_single_coating_full_size_sampled_rows():
+    """The 2.0 M DOF single-coating mirror (p = 6): sampled element rows of
+    A u against the oracle's element-by-element rows, FP64 and FP32."""
+    desc = W.single_coating()
+    ctx = gpu_ctx(desc)
+    m = Mesh(desc)
+    op = Operator(m)
+    u = W.random_field(desc, 11)
+    y = ctx.apply_operator(to_dev(u)).cpu().numpy()
+    y32 = ctx.apply_operator(to_dev(u, torch.float32)).cpu().numpy()
+    nl = 3 * m.n
+    rng = np.random.default_rng(0)
+    sample = sorted(set([0, m.ncol - 1, m.ncol, m.E - 1, 40, 80]
+                        + rng.integers(0, m.E, size=6).tolist()))
+    scale = 0.0
+    rows = {}
+    for e in sample:
+        rows[e] = op.apply_element(e, u)
+        scale = max(scale, np.max(np.abs(rows[e])))
+    for e in sample:
+        err = np.max(np.abs(y[e * nl:(e + 1) * nl] - rows[e])) / scale
+        assert err < 1e-11, (e, err)
+        err32 = np.max(np.abs(y32[e * nl:(e + 1) * nl] - rows[e])) / scale
+        assert err32 < 2e-5, (e, err32)
+
+
+def test_invalid_arguments_are_rejected_before_launch():
+    from paper_2111_06893_gb300 import thermonoise
+    desc = CASES["box_tiny_p2"]()
+    ctx = gpu_ctx(desc)
+    u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    lib = thermonoise.load()
+    assert lib.tn_apply_operator(ctx._h, 7, u.data_ptr(), u.data_ptr()) == thermonoise.TN_EINVAL_CODE
+    v = torch.zeros(ctx.ndof + 1, dtype=torch.float64, device="cuda")
+    assert lib.tn_apply_operator(ctx._h, 0, v[1:].data_ptr(), u.data_ptr()) == thermonoise.TN_EINVAL_CODE
+    bad = dict(desc)
+    bad["degree"] = 12
+    with pytest.raises(thermonoise.ThermonoiseError, match="TN_EINVAL"):
+        thermonoise.Context().build_mesh(bad)
+    with pytest.raises(thermonoise.ThermonoiseError, match="TN_ESTATE"):
+        c2 = thermonoise.Context()
+        c2.apply_operator(u)
