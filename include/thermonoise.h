@@ -57,7 +57,7 @@ enum { TN_BC_FREE = 0, TN_BC_FIXED = 1 };
 enum { TN_F64 = 0, TN_F32 = 1 };
 enum { TN_ISO = 0, TN_CUBIC = 1 };
 enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED_F32 = 1 };
-enum { TN_PC_JACOBI = 0 };
+enum { TN_PC_JACOBI = 0, TN_PC_ZLINE = 1 };
 
 typedef struct tn_ctx tn_ctx;
 
@@ -136,11 +136,29 @@ tn_status tn_rhs(tn_ctx *ctx, double *b_dev);
 /* diag(A) in FP64 (the Jacobi preconditioner). ndof values. */
 tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
 
+/* z = M^-1 r for a preconditioner of the Krylov solve (Sec. 2.3 accelerates
+ * its solver; these preconditioners replace its multigrid/Schwarz):
+ * TN_PC_JACOBI: M = diag(A).  TN_PC_ZLINE: M = the exact principal
+ * sub-matrix of A on every vertical line of nodes (one cross-section node of
+ * one column, all slabs, all nodes along zeta, three components), block
+ * tridiagonal over the slabs, factorised by block Cholesky (FP64) and stored
+ * in FP32 -- it captures the coupling across thin layers, whose elements
+ * have aspect ratios up to ~1e4.  The first call after tn_build_mesh /
+ * tn_set_materials builds the factors (2 * 3N^3 * n_slabs * 4 bytes per
+ * column-node line).  precision TN_F64 / TN_F32 selects double / float
+ * vectors r, z (caller-owned device buffers of tn_ndof() values, 16-byte
+ * aligned, not overlapping). */
+tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *r_dev, void *z_dev);
+
 /* Krylov solve of A u = b for the beam load (Sec. 2.3).
- * mode TN_SOLVE_F64: Jacobi-preconditioned CG in FP64.
+ * precond: TN_PC_JACOBI or TN_PC_ZLINE (see tn_precond_apply).
+ * mode TN_SOLVE_F64: preconditioned CG in FP64, restarted from the current
+ * iterate (true residual) if the recursive residual drifted.
  * mode TN_SOLVE_MIXED_F32: iterative refinement, FP64 residual b - A x and
  * update, inner Jacobi-PCG entirely in FP32 to inner_rtol.
- * Stops when ||b - A u||_2 <= rtol ||b||_2 (FP64 residual).  u_dev holds the
+ * Stops when ||b - A u||_2 <= rtol ||b||_2 (FP64 residual), or by the energy
+ * test of energy_rtol, or when the FP64 residual stagnates (thin layers put
+ * its rounding floor near eps64 * cond(A)); u_dev holds the
  * initial guess on entry if use_x0 != 0 (else it starts from 0) and the FP64
  * solution on exit.  Returns TN_ENOTCONV with the best iterate if max_iter
  * (total inner iterations) is reached. */
@@ -153,6 +171,10 @@ typedef struct {
   int max_outer;
   int use_x0;
   int check_every;          /* iterations between host convergence checks */
+  double energy_rtol;       /* > 0: also stop once every layer energy U_i
+                               changes by <= energy_rtol (relative) between
+                               two checks (refinement steps, or check_every
+                               FP64 iterations); 0: residual test only     */
 } tn_solve_opts;
 typedef struct {
   int status;
@@ -162,6 +184,7 @@ typedef struct {
   int applies_f32;
   int64_t launches;         /* kernel launches issued by this call         */
   double rel_residual;
+  double energy_change;     /* last max_i |dU_i / U_i| (energy test only)  */
   double seconds;
 } tn_solve_report;
 tn_status tn_solve(tn_ctx *ctx, const tn_solve_opts *opts, double *u_dev, tn_solve_report *rep);

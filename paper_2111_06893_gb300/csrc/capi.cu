@@ -3,6 +3,7 @@
 // orchestration of the solve, energies and PSD.
 #include <chrono>
 #include <cmath>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -10,6 +11,7 @@
 #include <new>
 
 #include "tn_internal.h"
+#include "tn_precond.h"
 #include "tn_solver.h"
 
 namespace {
@@ -63,9 +65,24 @@ struct tn_ctx {
   double *elem_energy = nullptr, *layer_energy = nullptr;
   size_t ws_E = 0;
   int ws_layers = 0;
+  // z-line preconditioner (valid while mesh and materials are unchanged)
+  float *zfac = nullptr;
+  double *zfac64 = nullptr;
+  double *zpart = nullptr;
+  int *zstatus = nullptr;
+  bool zready = false;
 };
 
+static void free_precond(tn_ctx *c) {
+  dfree(c->zfac);
+  dfree(c->zfac64);
+  dfree(c->zpart);
+  dfree(c->zstatus);
+  c->zready = false;
+}
+
 static void free_mesh(tn_ctx *c) {
+  free_precond(c);
   dfree(c->d_colgeo);
   dfree(c->d_slabgeo);
   dfree(c->d_colnb);
@@ -117,6 +134,67 @@ static tn_status ensure_ws(tn_ctx *c) {
   return TN_OK;
 }
 
+// builds the z-line factors on stream st (temporary FP64 blocks freed after)
+static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
+  if (c->zready) return TN_OK;
+  free_precond(c);
+  const size_t bb = tn_zline_block_bytes(c->dm), fb = tn_zline_factor_bytes(c->dm);
+  double *blk = nullptr;
+  cudaError_t e = cudaMalloc((void **)&blk, bb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac, fb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac64, 2 * fb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zpart, sizeof(double) * tn_zline_partials(c->dm));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zstatus, sizeof(int));
+  if (e != cudaSuccess) {
+    if (blk) cudaFree(blk);
+    free_precond(c);
+    cudaGetLastError();
+    return fail(TN_ENOMEM, "z-line preconditioner needs %.2f GB: %s", (bb + 3 * fb) / 1e9, cudaGetErrorString(e));
+  }
+  int status = 0;
+  e = cudaMemsetAsync(c->zstatus, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = tn_zline_setup(c->dm, blk, c->zfac, c->zfac64, c->zstatus, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->zstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(blk);
+  if (e != cudaSuccess) return cuda_fail(e, "z-line set-up");
+  if (status) return fail(TN_EBREAKDOWN, "z-line block not positive definite");
+  c->zready = true;
+  return TN_OK;
+}
+
+// energies of the current iterate and their largest relative change since the
+// previous call (for the energy stopping test)
+struct EnergyTrack {
+  tn_ctx *c;
+  const double *u;
+  cudaStream_t st;
+  double tol;
+  double prev[4096];
+  double cur[4096];
+  bool have_prev = false;
+  double change = INFINITY;
+  cudaError_t err = cudaSuccess;
+  bool step() {
+    const int nl = c->dm.n_layers;
+    err = tn_launch_energy(c->dm, u, c->elem_energy, c->layer_energy, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(cur, c->layer_energy, sizeof(double) * nl, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return true;
+    bool ok = have_prev;
+    double ch = 0.0;
+    for (int i = 0; i < nl && have_prev; ++i) {
+      const double d = std::fabs(cur[i] - prev[i]) / std::fabs(cur[i]);
+      ch = d > ch ? d : ch;
+    }
+    if (have_prev) change = ch;
+    for (int i = 0; i < nl; ++i) prev[i] = cur[i];
+    have_prev = true;
+    return ok && change <= tol;
+  }
+  static bool hook(void *self) { return static_cast<EnergyTrack *>(self)->step(); }
+};
+
 static tn_status need_ready(const tn_ctx *c, bool beam) {
   if (!c) return fail(TN_EINVAL, "null context");
   if (!c->have_mesh) return fail(TN_ESTATE, "no mesh: call tn_build_mesh first");
@@ -152,6 +230,7 @@ tn_status tn_create(tn_ctx **out, int device, void *cuda_stream) {
       std::memcpy(tabs.D[N], D, sizeof(double) * N * N);
     }
     e = tn_upload_lgl(&tabs);
+    if (e == cudaSuccess) e = tn_upload_lgl_precond(&tabs);
   }
   if (e != cudaSuccess) {
     tn_destroy(c);
@@ -257,6 +336,7 @@ tn_status tn_set_materials(tn_ctx *c, int n, const tn_material *mats) {
   if (e != cudaSuccess) return cuda_fail(e, "uploading materials");
   c->dm.layer_c = c->d_layer_c;
   c->have_mat = true;
+  free_precond(c);
   return TN_OK;
 }
 
@@ -312,9 +392,11 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
   if (!o) return fail(TN_EINVAL, "opts is null");
   if ((st = check_buf(c, u, 8, "u"))) return st;
   if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
-  if (o->precond != TN_PC_JACOBI) return fail(TN_EINVAL, "unknown preconditioner");
+  if (o->precond != TN_PC_JACOBI && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "unknown preconditioner");
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
   if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
+  if (!(o->energy_rtol >= 0.0)) return fail(TN_EINVAL, "energy_rtol must be >= 0");
+  if (c->hm.n_layers > 4096) return fail(TN_EINVAL, "at most 4096 layers");
   if (o->mode == TN_SOLVE_MIXED_F32 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0) || o->max_outer < 1))
     return fail(TN_EINVAL, "mixed mode needs 0 < inner_rtol < 1 and max_outer >= 1");
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
@@ -330,6 +412,11 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
   CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
   double bb = 0.0;
   CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
+  const bool zl = o->precond == TN_PC_ZLINE;
+  if (zl) {
+    tn_status zs = ensure_zline(c, s);
+    if (zs != TN_OK) return zs;
+  }
   tn_solve_report r{};
   tn_status result = TN_OK;
   if (bb == 0.0) {
@@ -337,17 +424,43 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
   } else if (o->mode == TN_SOLVE_F64) {
     CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv64, TN_F64, s), "dinv");
     PcgVectors v{u, c->r64, c->z64, c->p64, c->q64, c->b64, c->dinv64};
-    int applies = 0;
-    CU_TRY(tn::pcg_f64(c->dm, n, v, o->use_x0 == 0, o->rtol, o->max_iter, chunk, c->scal, c->scal_host,
-                       c->part_elem, c->part_red, s, &applies), "pcg f64");
-    r.inner_iters = c->scal_host->iters;
-    r.outer_iters = 1;
-    r.applies_f64 = applies;
-    if (c->scal_host->breakdown) result = fail(TN_EBREAKDOWN, "CG breakdown after %d iterations", r.inner_iters);
+    if (zl) { v.zfac = c->zfac64; v.part_rz = c->zpart; }
+    // FP64 PCG; restarted from the current iterate (true residual) if the
+    // recursively updated residual drifted away from b - A x
+    bool x0_zero = o->use_x0 == 0;
+    EnergyTrack et{c, u, s, o->energy_rtol};
+    ChunkHook hook;
+    if (o->energy_rtol > 0.0) { hook.fn = &EnergyTrack::hook; hook.user = &et; }
+    bool energy_done = false;
+    for (int restart = 0; restart < 4 && !energy_done; ++restart) {
+      int applies = 0;
+      CU_TRY(tn::pcg_f64(c->dm, n, v, x0_zero, o->rtol, o->max_iter - r.inner_iters, chunk, c->scal,
+                         c->scal_host, c->part_elem, c->part_red, s, &applies, hook), "pcg f64");
+      CU_TRY(et.err, "energy check");
+      energy_done = o->energy_rtol > 0.0 && et.have_prev && et.change <= o->energy_rtol;
+      r.energy_change = et.change;
+      r.inner_iters += c->scal_host->iters;
+      r.outer_iters += 1;
+      r.applies_f64 += applies;
+      if (c->scal_host->breakdown) {
+        result = fail(TN_EBREAKDOWN, "CG breakdown after %d iterations", r.inner_iters);
+        break;
+      }
+      double rr = 0.0;
+      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
+      r.applies_f64 += 1;
+      if (energy_done || std::sqrt(rr / bb) <= o->rtol || r.inner_iters >= o->max_iter) break;
+      x0_zero = false;
+    }
+    r.status = energy_done ? 1 : 0;
   } else {
     CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
     if (!o->use_x0) CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
     int total_inner = 0;
+    EnergyTrack et{c, u, s, o->energy_rtol};
+    double best = INFINITY;
+    int stall = 0;
+    bool energy_done = false;
     for (int outer = 0; outer < o->max_outer; ++outer) {
       double rr = 0.0;
       CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
@@ -355,10 +468,20 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
       r.rel_residual = std::sqrt(rr / bb);
       if (!std::isfinite(rr)) { result = fail(TN_EBREAKDOWN, "non-finite residual"); break; }
       if (r.rel_residual <= o->rtol) break;
+      if (o->energy_rtol > 0.0 && outer > 0) {
+        energy_done = et.step();
+        CU_TRY(et.err, "energy check");
+        r.energy_change = et.change;
+        if (energy_done) break;
+      }
+      // stagnation: the FP64 residual has reached its rounding floor
+      if (r.rel_residual < 0.5 * best) { best = r.rel_residual; stall = 0; }
+      else if (++stall >= 3) break;
       if (total_inner >= o->max_iter) break;
       const double rn = std::sqrt(rr);
       CU_TRY(tn::cast_scaled(n, c->r64, 1.0 / rn, c->b32, c->d32, s), "cast");
       PcgVectors v{c->d32, c->r32, c->z32, c->p32, c->q32, c->b32, c->dinv32};
+      if (zl) { v.zfac = c->zfac; v.part_rz = c->zpart; }
       int applies = 0;
       CU_TRY(tn::pcg_f32(c->dm, n, v, true, o->inner_rtol, o->max_iter - total_inner, chunk, c->scal,
                          c->scal_host, c->part_elem, c->part_red, s, &applies), "pcg f32");
@@ -372,14 +495,17 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
       CU_TRY(tn::refine_update(n, u, c->d32, rn, s), "refine");
     }
     r.inner_iters = total_inner;
+    r.status = energy_done ? 1 : 0;
   }
   // true FP64 residual of the returned iterate
+  const bool energy_ok = r.status == 1;
+  r.status = 0;
   if (bb != 0.0 && result == TN_OK) {
     double rr = 0.0;
     CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
     r.applies_f64 += 1;
     r.rel_residual = std::sqrt(rr / bb);
-    if (!(r.rel_residual <= o->rtol))
+    if (!(r.rel_residual <= o->rtol) && !energy_ok)
       result = fail(TN_ENOTCONV, "not converged: relative residual %.3e > %.3e after %d iterations",
                     r.rel_residual, o->rtol, r.inner_iters);
   }
@@ -391,6 +517,29 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
   r.launches = tn::g_launches;
   if (rep) *rep = r;
   return result;
+}
+
+tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r, void *z) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if (precision != TN_F64 && precision != TN_F32) return fail(TN_EINVAL, "precision must be TN_F64 or TN_F32");
+  if (precond != TN_PC_JACOBI && precond != TN_PC_ZLINE) return fail(TN_EINVAL, "unknown preconditioner");
+  const size_t es = precision == TN_F64 ? 8 : 4;
+  if ((st = check_buf(c, r, es, "r"))) return st;
+  if ((st = check_buf(c, z, es, "z"))) return st;
+  const char *a = (const char *)r, *b = (const char *)z;
+  if (a < b + c->ndof * es && b < a + c->ndof * es) return fail(TN_EINVAL, "r and z overlap");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  if (precond == TN_PC_ZLINE) {
+    if ((st = ensure_zline(c, c->stream))) return st;
+    CU_TRY(tn_zline_solve(c->dm, precision, precision == TN_F64 ? (const void *)c->zfac64 : (const void *)c->zfac,
+                          r, z, c->zpart, nullptr, c->stream), "z-line solve");
+    return TN_OK;
+  }
+  CU_TRY(tn_launch_diag(c->dm, c->diag64, c->stream), "diag");
+  CU_TRY(tn_jacobi_apply(c->ndof, precision, c->diag64, r, z, c->stream), "jacobi");
+  return TN_OK;
 }
 
 tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {

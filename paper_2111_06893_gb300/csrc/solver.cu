@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "tn_internal.h"
+#include "tn_precond.h"
 #include "tn_solver.h"
 
 namespace {
@@ -220,9 +221,94 @@ __global__ void k_invert(size_t n, const double *__restrict__ d, T *__restrict__
 }
 
 template <typename T>
+__global__ void k_jacobi(size_t n, const double *__restrict__ d, const T *__restrict__ r, T *__restrict__ z) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    z[t] = (T)((double)r[t] / d[t]);
+}
+
+template <typename T>
 __global__ void k_fill(size_t n, T *__restrict__ v, T val) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     v[t] = val;
+}
+
+
+// ---- variants for a preconditioner applied by a separate kernel (z-line)
+template <typename T>
+__global__ void k_update_r(tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__restrict__ r,
+                           const T *__restrict__ p, const T *__restrict__ q, double *part) {
+  if (s->done) return;
+  const T alpha = (T)s->alpha;
+  double rr = 0.0, dummy = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    x[t] += alpha * p[t];
+    const T rv = r[t] - alpha * q[t];
+    r[t] = rv;
+    rr += (double)rv * (double)rv;
+  }
+  block_sum2(rr, dummy);
+  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+__device__ void finish_beta(tn_pcg_scalars *s, double rz, double rr) {
+  s->iters += 1;
+  s->rr = rr;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    s->breakdown = 1;
+    s->done = 1;
+    return;
+  }
+  s->beta = rz / s->rz;
+  s->rz = rz;
+  if (rr <= s->tol2 || s->iters >= s->max_iters) s->done = 1;
+}
+
+__global__ void k_beta_split(tn_pcg_scalars *s, const double *rzp, int nrz, const double *rrp, int nrr) {
+  if (s->done) return;
+  double rz = 0.0, rr = 0.0;
+  for (int t = threadIdx.x; t < nrz; t += blockDim.x) rz += rzp[t];
+  for (int t = threadIdx.x; t < nrr; t += blockDim.x) rr += rrp[t];
+  block_sum2(rz, rr);
+  if (threadIdx.x == 0) finish_beta(s, rz, rr);
+}
+
+// r = b - Ax (or b), partial r.r
+template <typename T>
+__global__ void k_init_r(size_t n, const T *__restrict__ b, const T *__restrict__ Ax, T *__restrict__ r,
+                         double *part) {
+  double rr = 0.0, dummy = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const T rv = Ax ? b[t] - Ax[t] : b[t];
+    r[t] = rv;
+    rr += (double)rv * (double)rv;
+  }
+  block_sum2(rr, dummy);
+  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+template <typename T>
+__global__ void k_copy(size_t n, T *__restrict__ dst, const T *__restrict__ src) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+__global__ void k_init_scalars_split(tn_pcg_scalars *s, const double *rzp, int nrz, const double *rrp, int nrr,
+                                     double tol2_rel, int max_iters) {
+  double rz = 0.0, rr = 0.0;
+  for (int t = threadIdx.x; t < nrz; t += blockDim.x) rz += rzp[t];
+  for (int t = threadIdx.x; t < nrr; t += blockDim.x) rr += rrp[t];
+  block_sum2(rz, rr);
+  if (threadIdx.x == 0) {
+    s->rz = rz;
+    s->rr = rr;
+    s->rr0 = rr;
+    s->tol2 = tol2_rel * rr;
+    s->iters = 0;
+    s->max_iters = max_iters;
+    s->breakdown = 0;
+    s->done = (rr == 0.0 || rr <= s->tol2) ? 1 : 0;
+    s->alpha = s->beta = s->pq = 0.0;
+  }
 }
 
 }  // namespace
@@ -264,26 +350,53 @@ static cudaError_t pcg_iteration(const DevMesh &m, int prec, size_t n, PcgVector
   return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t pcg_iteration_zline(const DevMesh &m, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
+                                       double *part_elem, double *part_red, cudaStream_t st) {
+  TN_CU(tn_launch_apply(m, prec, v.p, v.q, part_elem, nullptr, st));
+  k_alpha<<<1, 256, 0, st>>>(s, part_elem, m.E);
+  TN_CU(cudaGetLastError());
+  k_update_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (const T *)v.p, (const T *)v.q,
+                                                    part_red);
+  TN_CU(cudaGetLastError());
+  TN_CU(tn_zline_solve(m, prec, v.zfac, v.r, v.z, v.part_rz, &s->done, st));
+  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, tn_zline_partials(m), part_red, kRedBlocks);
+  TN_CU(cudaGetLastError());
+  k_pupdate<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
+  return cudaGetLastError();
+}
+
 // PCG on A x = b in precision T; x holds the initial guess (x0_zero: x = 0).
 // Records `chunk` iterations in a graph and replays it until done.
 template <typename T>
 static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, bool x0_zero, double rtol,
                            int max_iters, int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host,
-                           double *part_elem, double *part_red, cudaStream_t st, int *applies) {
-  g_launches += x0_zero ? 3 : 3;
+                           double *part_elem, double *part_red, cudaStream_t st, int *applies,
+                           ChunkHook hook = ChunkHook()) {
+  const bool zl = v.zfac != nullptr;
+  g_launches += zl ? 6 : 3;
   if (x0_zero) {
     k_fill<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.x, T(0));
     TN_CU(cudaGetLastError());
-    k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, nullptr, (T *)v.r, (T *)v.z, (T *)v.p,
-                                                  (const T *)v.dinv, part_red);
   } else {
     TN_CU(tn_launch_apply(m, prec, v.x, v.q, nullptr, nullptr, st));
     *applies += 1;
-    k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, (const T *)v.q, (T *)v.r, (T *)v.z,
-                                                  (T *)v.p, (const T *)v.dinv, part_red);
   }
-  TN_CU(cudaGetLastError());
-  k_init_scalars<<<1, 256, 0, st>>>(s_dev, part_red, kRedBlocks, rtol * rtol, max_iters);
+  const T *Ax = x0_zero ? nullptr : (const T *)v.q;
+  if (zl) {
+    k_init_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, part_red);
+    TN_CU(cudaGetLastError());
+    TN_CU(tn_zline_solve(m, prec, v.zfac, v.r, v.z, v.part_rz, nullptr, st));
+    k_copy<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.p, (const T *)v.z);
+    TN_CU(cudaGetLastError());
+    k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, tn_zline_partials(m), part_red, kRedBlocks,
+                                            rtol * rtol, max_iters);
+  } else {
+    k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, (T *)v.z, (T *)v.p,
+                                                  (const T *)v.dinv, part_red);
+    TN_CU(cudaGetLastError());
+    k_init_scalars<<<1, 256, 0, st>>>(s_dev, part_red, kRedBlocks, rtol * rtol, max_iters);
+  }
   TN_CU(cudaGetLastError());
   TN_CU(cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st));
   TN_CU(cudaStreamSynchronize(st));
@@ -294,7 +407,8 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
   TN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t cap = cudaSuccess;
   for (int it = 0; it < chunk && cap == cudaSuccess; ++it)
-    cap = pcg_iteration<T>(m, prec, n, v, s_dev, part_elem, part_red, st);
+    cap = zl ? pcg_iteration_zline<T>(m, prec, n, v, s_dev, part_elem, part_red, st)
+             : pcg_iteration<T>(m, prec, n, v, s_dev, part_elem, part_red, st);
   cudaError_t endc = cudaStreamEndCapture(st, &graph);
   if (cap != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cap; }
   TN_CU(endc);
@@ -302,7 +416,7 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
   cudaGraphDestroy(graph);
   TN_CU(err);
   for (;;) {
-    g_launches += 5LL * chunk;
+    g_launches += (zl ? 6LL : 5LL) * chunk;
     err = cudaGraphLaunch(exec, st);
     if (err != cudaSuccess) break;
     err = cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st);
@@ -310,6 +424,7 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) break;
     if (s_host->done) break;
+    if (hook.fn && hook.fn(hook.user)) break;
   }
   cudaGraphExecDestroy(exec);
   *applies += s_host->iters;
@@ -318,9 +433,9 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
 
 cudaError_t pcg_f64(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
-                    double *part_red, cudaStream_t st, int *applies) {
+                    double *part_red, cudaStream_t st, int *applies, ChunkHook hook) {
   return pcg_run<double>(m, TN_F64, n, v, x0_zero, rtol, max_iters, chunk, s_dev, s_host, part_elem,
-                         part_red, st, applies);
+                         part_red, st, applies, hook);
 }
 
 cudaError_t pcg_f32(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
@@ -379,5 +494,15 @@ cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st) {
 }
 
 int reduction_blocks() { return kRedBlocks; }
+
+}  // namespace tn
+
+cudaError_t tn_jacobi_apply(size_t n, int prec, const double *diag, const void *r, void *z, cudaStream_t st) {
+  if (prec == TN_F64) k_jacobi<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (const double *)r, (double *)z);
+  else k_jacobi<float><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (const float *)r, (float *)z);
+  return cudaGetLastError();
+}
+
+namespace tn {
 
 }  // namespace tn

@@ -1,0 +1,16 @@
+// Column-line block preconditioner (precond.cu).
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+size_t tn_zline_block_bytes(const DevMesh &m);   // FP64 set-up blocks
+size_t tn_zline_factor_bytes(const DevMesh &m);  // FP32 factors kept for the solve
+int tn_zline_partials(const DevMesh &m);         // partial sums written by one solve
+cudaError_t tn_zline_setup(const DevMesh &m, double *blk, float *fac, double *fac64, int *status,
+                           cudaStream_t st);
+cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, const void *r, void *z, double *part,
+                           const int *done, cudaStream_t st);
+cudaError_t tn_upload_lgl_precond(const LglTables *t);

@@ -16,6 +16,16 @@ struct tn_pcg_scalars {
 struct PcgVectors {
   void *x, *r, *z, *p, *q;
   const void *b, *dinv;
+  const void *zfac = nullptr;   // z-line factors of the run's precision (nullptr: Jacobi)
+  double *part_rz = nullptr;    // partial r.z of the z-line solve
+};
+
+cudaError_t tn_jacobi_apply(size_t n, int prec, const double *diag, const void *r, void *z, cudaStream_t st);
+
+// called on the host after every replayed chunk; returns true to stop the run
+struct ChunkHook {
+  bool (*fn)(void *user) = nullptr;
+  void *user = nullptr;
 };
 
 namespace tn {
@@ -25,7 +35,7 @@ cudaError_t pcg_setup_dinv(const DevMesh &m, size_t n, const double *diag, void 
                            cudaStream_t st);
 cudaError_t pcg_f64(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
-                    double *part_red, cudaStream_t st, int *applies);
+                    double *part_red, cudaStream_t st, int *applies, ChunkHook hook = ChunkHook());
 cudaError_t pcg_f32(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
                     double *part_red, cudaStream_t st, int *applies);

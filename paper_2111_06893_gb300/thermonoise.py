@@ -20,14 +20,15 @@ TN_BC_FREE, TN_BC_FIXED = 0, 1
 TN_F64, TN_F32 = 0, 1
 TN_ISO, TN_CUBIC = 0, 1
 TN_SOLVE_F64, TN_SOLVE_MIXED_F32 = 0, 1
-TN_PC_JACOBI = 0
+TN_PC_JACOBI, TN_PC_ZLINE = 0, 1
+PRECONDS = {"jacobi": TN_PC_JACOBI, "zline": TN_PC_ZLINE}
 STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_ENOTCONV",
           -5: "TN_EBREAKDOWN", -6: "TN_ETIMEOUT", -7: "TN_ESTATE"}
 
 # every entry point declared in include/thermonoise.h
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
-           "tn_solve", "tn_layer_energies", "tn_noise_psd"]
+           "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply"]
 
 
 class MeshDesc(C.Structure):
@@ -48,13 +49,13 @@ class Material(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
-                ("use_x0", C.c_int), ("check_every", C.c_int)]
+                ("use_x0", C.c_int), ("check_every", C.c_int), ("energy_rtol", C.c_double)]
 
 
 class SolveReport(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
                 ("applies_f64", C.c_int), ("applies_f32", C.c_int), ("launches", C.c_int64),
-                ("rel_residual", C.c_double),
+                ("rel_residual", C.c_double), ("energy_change", C.c_double),
                 ("seconds", C.c_double)]
 
     def as_dict(self):
@@ -93,6 +94,7 @@ def load():
         "tn_solve": (C.c_int, [vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
         "tn_layer_energies": (C.c_int, [vp, vp, dp]),
         "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
+        "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,13 +231,26 @@ class Context:
         _check(load().tn_diagonal(self._h, C.c_void_p(out.data_ptr())))
         return out
 
-    def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-5, max_iter=200000, max_outer=50,
-              x0=None, check_every=25, out=None, raise_on_error=True):
+    def precond_apply(self, r, z=None, precond="zline"):
+        torch = self._torch
+        prec = TN_F64 if r.dtype == torch.float64 else TN_F32
+        if z is None:
+            z = torch.empty_like(r)
+        self._check_tensor(r, r.dtype, "r")
+        self._check_tensor(z, r.dtype, "z")
+        _check(load().tn_precond_apply(self._h, PRECONDS[precond], prec, C.c_void_p(r.data_ptr()),
+                                       C.c_void_p(z.data_ptr())))
+        return z
+
+    def solve(self, mode="f64", rtol=1e-12, inner_rtol=0.05, max_iter=200000, max_outer=60,
+              x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",
+              energy_rtol=0.0):
         o = SolveOpts()
         o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
-        o.precond = TN_PC_JACOBI
+        o.precond = PRECONDS[precond]
         o.rtol, o.inner_rtol = rtol, inner_rtol
         o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
+        o.energy_rtol = energy_rtol
         u = out if out is not None else self._vec(self._torch.float64)
         o.use_x0 = 0
         if x0 is not None:

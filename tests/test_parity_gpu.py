@@ -92,13 +92,52 @@ def test_energies_match_oracle_on_random_field(name):
     assert np.max(np.abs(U - Uo) / np.abs(Uo)) < 1e-12
 
 
+def line_index_sets(m):
+    """DOF indices of every vertical line of nodes: column c, cross-section
+    node (i, j), all slabs top-down, three components, all k (the ordering
+    inside a line does not matter for the block solve)."""
+    N, n = m.N, m.n
+    sets = []
+    for c in range(m.ncol):
+        for j in range(N):
+            for i in range(N):
+                idx = [((s * m.ncol + c) * 3 + comp) * n + (k * N + j) * N + i
+                       for s in range(m.nslab) for comp in range(3) for k in range(N)]
+                sets.append(np.array(idx))
+    return sets
+
+
+@pytest.mark.parametrize("name", ["box_layers_p4", "cyl_small_p4_k2", "cyl_thin_p5", "cyl_small_p7_k1_fixed"])
+def test_zline_preconditioner_matches_oracle_line_blocks(name):
+    """z = A_LL^-1 r on every vertical line, A_LL the principal sub-matrix of
+    the oracle's assembled operator on the line's DOFs."""
+    desc, op, A = oracle_case(name)
+    A = A.tocsr()
+    ctx = gpu_ctx(desc)
+    r = W.random_field(desc, 21)
+    z = ctx.precond_apply(to_dev(r), precond="zline").cpu().numpy()
+    z32 = ctx.precond_apply(to_dev(r, torch.float32), precond="zline").cpu().numpy().astype(np.float64)
+    worst_bwd = worst_fwd = worst32 = 0.0
+    for S in line_index_sets(op.mesh):
+        B = A[S][:, S].toarray()
+        zo = np.linalg.solve(B, r[S])
+        scale = np.abs(B).max() * np.abs(z[S]).max()
+        worst_bwd = max(worst_bwd, np.abs(B @ z[S] - r[S]).max() / scale)
+        worst32 = max(worst32, np.abs(B @ z32[S] - r[S]).max() / (np.abs(B).max() * np.abs(z32[S]).max()))
+        worst_fwd = max(worst_fwd, np.abs(z[S] - zo).max() / np.abs(zo).max())
+    assert worst_bwd < 1e-13, worst_bwd
+    assert worst32 < 1e-5, worst32
+    assert worst_fwd < 1e-6, worst_fwd
+
+
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
-def test_solve_plain_box_energies_match_oracle_direct_solve(mode):
+@pytest.mark.parametrize("precond", ["jacobi", "zline"])
+def test_solve_plain_box_energies_match_oracle_direct_solve(mode, precond):
     desc, op, A = oracle_case("plain_box")
     uo = ob.solve_dense(A, op.rhs())
     Uo = ob.layer_energies(op, uo)
     ctx = gpu_ctx(desc)
-    u, rep = ctx.solve(mode=mode, rtol=1e-13)
+    u, rep = ctx.solve(mode=mode, rtol=1e-13, precond=precond)
     assert rep["rel_residual"] <= 1e-13
     U = ctx.layer_energies(u)
     assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (U, Uo)
@@ -114,9 +153,9 @@ def test_solve_layered_cylinder_matches_oracle():
     Uo = ob.layer_energies(op, uo)
     ctx = gpu_ctx(desc)
     for mode in ("f64", "mixed"):
-        u, rep = ctx.solve(mode=mode, rtol=1e-13)
+        u, rep = ctx.solve(mode=mode, rtol=1e-13, energy_rtol=1e-12)
         U = ctx.layer_energies(u)
-        assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (mode, U, Uo)
+        assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (mode, U, Uo, rep)
     from paper_2111_06893_gb300 import noise_psd
     phi = [1e-4, 4e-4, 1e-6]
     S = noise_psd(U, phi, 4.14e-21, 100.0, desc["beam"]["F0"])
