@@ -195,6 +195,29 @@ tn_status tn_solve(tn_ctx *ctx, const tn_solve_opts *opts, double *u_dev, tn_sol
  * n_layers doubles (coating layers top-down, substrate last).  Synchronises. */
 tn_status tn_layer_energies(tn_ctx *ctx, const double *u_dev, double *U_host);
 
+/* Adjoint gradient of J = sum_i w_i U_i (energies of tn_layer_energies) for
+ * the solution u of A u = b (caller-owned FP64 device buffer, e.g. from
+ * tn_solve).  Because the weak-form operator is symmetric the adjoint
+ * A lambda = g, g = dJ/du = sum_i w_i K_i u (K_i the energy matrix of layer
+ * i), is solved with the same operator, preconditioner and solver (opts;
+ * energy_rtol is ignored).  Then, for every parameter theta,
+ *   dJ/dtheta = 1/2 u^T (sum_i w_i dK_i/dtheta) u + lambda^T (db/dtheta - dA/dtheta u),
+ * with dA/dtheta u and dK_i/dtheta formed exactly by forward-mode (dual
+ * number) versions of the operator and energy kernels.  Parameters:
+ *   dJ_dslab_z[n_slabs + 1]  slab boundary positions slab_z[s] (the top,
+ *                            s = 0, is held at z = 0 and returns 0);
+ *                            layer thicknesses follow by the chain rule
+ *   dJ_dr0[1]                beam width r0 (only b depends on it)
+ *   dJ_dmat[3 n_layers]      c11, c12, c44 of every layer (isotropic layers:
+ *                            c11 = lambda + 2 mu, c12 = lambda, c44 = mu)
+ * w_host: n_layers weights (host).  lambda_dev: optional ndof FP64 device
+ * buffer receiving the adjoint solution (NULL: internal).  All outputs are
+ * host arrays.  Returns the adjoint solve's status (TN_ENOTCONV keeps the
+ * gradients of the best adjoint iterate).  Synchronises. */
+tn_status tn_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const double *u_dev, const double *w_host,
+                         double *lambda_dev, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                         tn_solve_report *rep);
+
 /* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
  * per layer, dissipated power 2 pi f sum_i phi_i U_i):
  *   S_out = 4 kB_T sum_i phi_i U_i / (pi f F0^2).  Host only. */

@@ -49,7 +49,8 @@ class Operator:
         self.Dlog = [np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)),
                      np.kron(D, np.kron(I, I))]
         self.Y = [materials.tensor(m) for m in mesh.desc["materials"]]
-        self.C = float(mesh.desc["penalty_C"])
+        self.C = mesh.desc["penalty_C"]
+        self.dtype = np.result_type(mesh.slab_z, *[Y.dtype for Y in self.Y], mesh.desc["beam"]["r0"], float)
         self._G = {}
 
     # ------------------------------------------------------------ pieces
@@ -74,7 +75,7 @@ class Operator:
         wJ = self.mesh.geometry(e)["wJ"]
         Y = self.Ye(e)
         n = self.mesh.n
-        K = np.zeros((3, n, 3, n))
+        K = np.zeros((3, n, 3, n), dtype=self.dtype)
         for a in range(3):
             for b in range(3):
                 Mab = G[a].T @ (wJ[:, None] * G[b])
@@ -98,7 +99,7 @@ class Operator:
         G = self.grad_matrices(e)
         Y = self.Ye(e)
         n, m = self.mesh.n, len(F)
-        Tr = np.zeros((3, m, 3, n))
+        Tr = np.zeros((3, m, 3, n), dtype=self.dtype)
         for j in range(3):
             for l in range(3):
                 for b in range(3):
@@ -111,7 +112,7 @@ class Operator:
         """Pen[(j,q),(l,q)] = sigma(q) n_a Y_*^{ajbl} n_b."""
         m = len(sigma)
         Mq = np.einsum("qa,ajbl,qb->qjl", nvec, Ystar, nvec) * sigma[:, None, None]
-        P = np.zeros((3, m, 3, m))
+        P = np.zeros((3, m, 3, m), dtype=self.dtype)
         for j in range(3):
             for l in range(3):
                 P[j, np.arange(m), l, np.arange(m)] = Mq[:, j, l]
@@ -174,7 +175,7 @@ class Operator:
     def apply_element(self, e, u):
         """Rows of element e of A u, without assembling the rest."""
         nloc = 3 * self.mesh.n
-        y = np.zeros(nloc)
+        y = np.zeros(nloc, dtype=np.result_type(self.dtype, u))
         for e2, B in self.element_rows(e).items():
             y += B @ u[e2 * nloc:(e2 + 1) * nloc]
         return y
@@ -189,9 +190,9 @@ class Operator:
         beam = mesh.desc["beam"]
         r0, F0 = beam["r0"], beam["F0"]
         nloc = 3 * mesh.n
-        b = np.zeros(mesh.ndof)
+        b = np.zeros(mesh.ndof, dtype=self.dtype)
         for e in range(mesh.E):
-            be = np.zeros(nloc)
+            be = np.zeros(nloc, dtype=self.dtype)
             for f in range(6):
                 bc = mesh.boundary_condition(e, f)
                 if bc == "interior":

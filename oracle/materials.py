@@ -34,7 +34,7 @@ def iso_tensor(lam, mu):
 
 
 def cubic_tensor(c11, c12, c44):
-    Y = np.zeros((3, 3, 3, 3))
+    Y = np.zeros((3, 3, 3, 3), dtype=np.result_type(c11, c12, c44, float))
     for i in range(3):
         for j in range(3):
             for k in range(3):

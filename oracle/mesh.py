@@ -12,6 +12,13 @@ Neighbours are found from physical coordinates (face centres and face nodes),
 not from the element numbering, and boundary faces are classified by where
 they lie (top z = 0, bottom, sides).
 
+Every element map here is a cross-section map (X, Y)(xi, eta) times a
+vertical map Z(zeta).  ``geometry`` takes the 2x2 cross-section Jacobian by
+complex step and dZ/dzeta from its closed form, so that the whole oracle stays
+analytic in the slab positions and can itself be differentiated by complex
+step (gradients); ``jacobian`` (full 3-D complex step) pins the two against
+each other.
+
 Test infrastructure: slow, plain FP64, imported only by tests and by the
 CPU-baseline leg of the benchmark.
 """
@@ -52,7 +59,7 @@ class Mesh:
             self.ncol = 9 * self.k ** 2
         else:
             raise ValueError(desc["kind"])
-        self.slab_z = np.asarray(desc["slab_z"], dtype=float)
+        self.slab_z = np.asarray(desc["slab_z"])
         self.nslab = len(self.slab_z) - 1
         self.E = self.ncol * self.nslab
         self.ndof = 3 * self.n * self.E
@@ -105,6 +112,15 @@ class Mesh:
             return -np.exp(0.5 * (1 + zeta) * np.log(st) + 0.5 * (1 - zeta) * np.log(sb))
         return 0.5 * (1 + zeta) * zt + 0.5 * (1 - zeta) * zb
 
+    def _dmap_z(self, s, zeta):
+        """dZ/dzeta of the slab map, written out."""
+        zt, zb = self.slab_z[s], self.slab_z[s + 1]
+        if self.desc["slab_log"][s]:
+            st, sb = -zt, -zb
+            depth = np.exp(0.5 * (1 + zeta) * np.log(st) + 0.5 * (1 - zeta) * np.log(sb))
+            return 0.5 * depth * (np.log(sb) - np.log(st))
+        return 0.5 * (zt - zb) + 0.0 * zeta
+
     def map(self, e, xi):
         """x(xi) for element e; xi has shape (..., 3); works for complex xi."""
         s, c = self.element_of(e)
@@ -122,12 +138,33 @@ class Mesh:
             cols.append(np.imag(self.map(e, xi + dx)) / _CSTEP)
         return np.stack(cols, axis=-1)
 
+    def jacobian_split(self, e, xi):
+        """J from a complex step of the cross-section map and dZ/dzeta."""
+        s, c = self.element_of(e)
+        xi = np.asarray(xi, dtype=float)
+        J = np.zeros(xi.shape[:-1] + (3, 3), dtype=np.result_type(self.slab_z, float))
+        for m_ in range(2):
+            d = np.zeros(3, dtype=complex)
+            d[m_] = 1j * _CSTEP
+            xc = xi + d
+            X, Y = self._map_xy(c, xc[..., 0], xc[..., 1])
+            J[..., 0, m_] = np.imag(X) / _CSTEP
+            J[..., 1, m_] = np.imag(Y) / _CSTEP
+        J[..., 2, 2] = self._dmap_z(s, xi[..., 2])
+        return J
+
     def geometry(self, e):
         """Nodal coordinates, Jacobian, det, inverse and quadrature weight w detJ."""
         if e in self._geo:
             return self._geo[e]
-        xyz = np.real(self.map(e, self.xi_nodes.astype(complex)))
-        J = self.jacobian(e, self.xi_nodes)
+        xi = self.xi_nodes
+        s, c = self.element_of(e)
+        X, Y = self._map_xy(c, xi[:, 0], xi[:, 1])
+        Z = self._map_z(s, xi[:, 2])
+        xyz = np.stack(np.broadcast_arrays(X, Y, Z), axis=-1)
+        if not np.iscomplexobj(self.slab_z):
+            xyz = np.real(xyz)
+        J = self.jacobian_split(e, xi)
         detJ = np.linalg.det(J)
         Jinv = np.linalg.inv(J)  # Jinv[p, m, a] = dxi^m / dx^a
         geo = {"xyz": xyz, "J": J, "detJ": detJ, "Jinv": Jinv,
@@ -158,7 +195,7 @@ class Mesh:
         d, s = divmod(f, 2)
         F = self.face_nodes(f)
         row = geo["Jinv"][F, d, :]  # grad xi^d
-        mag = np.linalg.norm(row, axis=1)
+        mag = np.sqrt(np.sum(row * row, axis=1))
         sign = 1.0 if s else -1.0
         n = sign * row / mag[:, None]
         Jsig = geo["detJ"][F] * mag
@@ -175,6 +212,7 @@ class Mesh:
                 xi[d] = 1.0 if s else -1.0
                 centres[e, f] = np.real(self.map(e, xi))
         flat = centres.reshape(-1, 3)
+        flat = np.real(flat)
         scale = max(1.0, float(np.max(np.abs(flat))))
         tree = cKDTree(flat)
         pairs = tree.query_pairs(r=1e-9 * scale, output_type="ndarray")
@@ -189,7 +227,7 @@ class Mesh:
                 raise RuntimeError("non-conforming face")
             self.neighbour[ea, fa], self.nb_face[ea, fa] = eb, fb
             self.neighbour[eb, fb], self.nb_face[eb, fb] = ea, fa
-        zmax, zmin = self.slab_z[0], self.slab_z[-1]
+        zmax, zmin = np.real(self.slab_z[0]), np.real(self.slab_z[-1])
         tol = 1e-9 * scale
         self.bkind = np.full((self.E, 6), "", dtype=object)
         for e in range(self.E):
@@ -212,8 +250,8 @@ class Mesh:
         if key in self._perm:
             return self._perm[key]
         e2, f2 = int(self.neighbour[e, f]), int(self.nb_face[e, f])
-        x1 = self.geometry(e)["xyz"][self.face_nodes(f)]
-        x2 = self.geometry(e2)["xyz"][self.face_nodes(f2)]
+        x1 = np.real(self.geometry(e)["xyz"][self.face_nodes(f)])
+        x2 = np.real(self.geometry(e2)["xyz"][self.face_nodes(f2)])
         dist, perm = cKDTree(x2).query(x1)
         scale = max(1.0, float(np.max(np.abs(x1))))
         if np.max(dist) > 1e-9 * scale or len(set(perm.tolist())) != len(perm):

@@ -38,12 +38,12 @@ def element_energy(op, e, u):
     grad = np.stack([G[a] @ ue.T for a in range(3)], axis=1)  # (n, a, l) = du_l/dx^a
     S = 0.5 * (grad + grad.transpose(0, 2, 1))
     dens = np.einsum("pij,ijkl,pkl->p", S, op.Ye(e), S)
-    return 0.5 * float(np.sum(mesh.geometry(e)["wJ"] * dens))
+    return 0.5 * np.sum(mesh.geometry(e)["wJ"] * dens)
 
 
 def layer_energies(op, u):
     """U_i per layer id (coating layers top-down, the substrate last)."""
-    U = np.zeros(op.mesh.n_layers)
+    U = np.zeros(op.mesh.n_layers, dtype=np.result_type(op.dtype, u))
     for e in range(op.mesh.E):
         U[op.mesh.layer(e)] += element_energy(op, e, u)
     return U
@@ -89,7 +89,10 @@ def solve_cg(op, A, b, rtol=1e-12, maxiter=20000):
 
 
 def solve_dense(A, b):
-    """A u = b by dense Cholesky (fails loudly if A is not positive definite)."""
+    """A u = b by dense Cholesky (fails loudly if A is not positive definite);
+    complex-symmetric systems (complex-step derivatives) by dense LU."""
     import scipy.linalg as sl
+    if np.iscomplexobj(A.data) or np.iscomplexobj(b):
+        return sl.lu_solve(sl.lu_factor(A.toarray(), check_finite=False), b)
     c = sl.cho_factor(A.toarray(), lower=True, overwrite_a=True, check_finite=False)
     return sl.cho_solve(c, b)

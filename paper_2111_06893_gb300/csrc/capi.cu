@@ -52,6 +52,8 @@ struct tn_ctx {
   DevMesh dm{};
   double *d_colgeo = nullptr, *d_slabgeo = nullptr, *d_layer_c = nullptr;
   int *d_colnb = nullptr, *d_colnbf = nullptr, *d_slab_layer = nullptr;
+  double *slab_z_host = nullptr;
+  int *slab_log_host = nullptr;
   double r0 = 1.0, F0 = 1.0;
   size_t ndof = 0;
   // workspace
@@ -89,6 +91,10 @@ static void free_mesh(tn_ctx *c) {
   dfree(c->d_colnbf);
   dfree(c->d_slab_layer);
   tn::free_host_mesh(&c->hm);
+  std::free(c->slab_z_host);
+  std::free(c->slab_log_host);
+  c->slab_z_host = nullptr;
+  c->slab_log_host = nullptr;
   c->have_mesh = false;
 }
 
@@ -280,6 +286,14 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
     free_mesh(c);
     return cuda_fail(e, "uploading the mesh");
   }
+  c->slab_z_host = (double *)std::malloc(sizeof(double) * (hm.nslab + 1));
+  c->slab_log_host = (int *)std::malloc(sizeof(int) * hm.nslab);
+  if (!c->slab_z_host || !c->slab_log_host) {
+    free_mesh(c);
+    return fail(TN_ENOMEM, "host allocation failed");
+  }
+  std::memcpy(c->slab_z_host, d->slab_z, sizeof(double) * (hm.nslab + 1));
+  std::memcpy(c->slab_log_host, d->slab_log, sizeof(int) * hm.nslab);
   DevMesh &m = c->dm;
   m.N = hm.N; m.p = hm.p; m.E = hm.E; m.ncol = hm.ncol; m.nslab = hm.nslab; m.n_layers = hm.n_layers;
   m.bc_side = hm.bc_side; m.bc_bottom = hm.bc_bottom; m.penC = hm.penC;
@@ -386,9 +400,19 @@ tn_status tn_diagonal(tn_ctx *c, double *d) {
   return TN_OK;
 }
 
+static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs, double *u,
+                            tn_solve_report *rep);
+
 tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report *rep) {
   tn_status st = need_ready(c, true);
   if (st) return st;
+  return solve_impl(c, o, nullptr, u, rep);
+}
+
+// A u = rhs (rhs == nullptr: the beam load); u, rhs device FP64
+static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs, double *u,
+                            tn_solve_report *rep) {
+  tn_status st = TN_OK;
   if (!o) return fail(TN_EINVAL, "opts is null");
   if ((st = check_buf(c, u, 8, "u"))) return st;
   if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
@@ -408,7 +432,8 @@ tn_status tn_solve(tn_ctx *c, const tn_solve_opts *o, double *u, tn_solve_report
   CU_TRY(cudaEventRecord(c->ev_in, c->stream), "event");
   CU_TRY(cudaStreamWaitEvent(s, c->ev_in, 0), "event wait");
   const size_t n = c->ndof;
-  CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, c->b64, s), "rhs");
+  if (rhs) CU_TRY(cudaMemcpyAsync(c->b64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "rhs copy");
+  else CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, c->b64, s), "rhs");
   CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
   double bb = 0.0;
   CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
@@ -540,6 +565,138 @@ tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r,
   CU_TRY(tn_launch_diag(c->dm, c->diag64, c->stream), "diag");
   CU_TRY(tn_jacobi_apply(c->ndof, precision, c->diag64, r, z, c->stream), "jacobi");
   return TN_OK;
+}
+
+
+// d(dz/dzeta)/d(z_s) at every node of slab q, for the slab boundary s
+// (slab q = s - 1 has z_bot = z_s, slab q = s has z_top = z_s)
+static void slab_seed(const tn::HostMesh &hm, const double *slab_z, const int *slab_log, int s, double *seed) {
+  const int N = hm.N;
+  double x[TN_MAX_N], w[TN_MAX_N], D[TN_MAX_N * TN_MAX_N];
+  tn::lgl(N, x, w, D);
+  for (int q = 0; q < hm.nslab * N; ++q) seed[q] = 0.0;
+  for (int q = s - 1; q <= s; ++q) {
+    if (q < 0 || q >= hm.nslab) continue;
+    const bool top = (q == s);  // z_s is the top of slab q
+    const double zt = slab_z[q], zb = slab_z[q + 1];
+    for (int k = 0; k < N; ++k) {
+      double d;
+      if (slab_log[q]) {
+        const double dt = -zt, db = -zb, a = 0.5 * (1 + x[k]), b = 0.5 * (1 - x[k]);
+        const double S = std::exp(a * std::log(dt) + b * std::log(db)), L = std::log(db) - std::log(dt);
+        // dz/dzeta = S L / 2;  d/dz = -d/d(depth)
+        d = top ? -0.5 * (S * a / dt * L - S / dt) : -0.5 * (S * b / db * L + S / db);
+      } else {
+        d = top ? 0.5 : -0.5;
+      }
+      seed[(size_t)q * N + k] = d;
+    }
+  }
+}
+
+static double host_sum(const double *dev, int n, double *tmp, cudaStream_t st, cudaError_t *err) {
+  *err = cudaMemcpyAsync(tmp, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += tmp[i];
+  return s;
+}
+
+tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, const double *w_host,
+                         double *lambda, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                         tn_solve_report *rep) {
+  tn_status st = need_ready(c, true);
+  if (st) return st;
+  if (!o || !w_host || !dJ_dslab_z || !dJ_dr0 || !dJ_dmat) return fail(TN_EINVAL, "null argument");
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (lambda && (st = check_buf(c, lambda, 8, "lambda"))) return st;
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  const tn::HostMesh &hm = c->hm;
+  const int S = hm.nslab, nl = hm.n_layers, N = hm.N;
+  const size_t n = c->ndof, E = (size_t)hm.E;
+  double *wdev = nullptr, *g = nullptr, *lam = lambda, *part = nullptr, *seed_dev = nullptr, *matseed = nullptr;
+  double *tmp = (double *)std::malloc(sizeof(double) * (E + 1024));
+  double *seed = (double *)std::malloc(sizeof(double) * (size_t)S * N);
+  double *sz = (double *)std::malloc(sizeof(double) * (S + 1));
+  int *slog = (int *)std::malloc(sizeof(int) * S);
+  cudaError_t e = (tmp && seed && sz && slog) ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&wdev, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&g, sizeof(double) * n);
+  if (e == cudaSuccess && !lam) e = cudaMalloc((void **)&lam, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * (E + 1024));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * (size_t)S * N);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 3 * nl);
+  tn_solve_report r{};
+  cudaStream_t s = c->stream;
+  auto cleanup = [&]() {
+    if (wdev) cudaFree(wdev);
+    if (g) cudaFree(g);
+    if (lam && lam != lambda) cudaFree(lam);
+    if (part) cudaFree(part);
+    if (seed_dev) cudaFree(seed_dev);
+    if (matseed) cudaFree(matseed);
+    std::free(tmp); std::free(seed); std::free(sz); std::free(slog);
+  };
+  if (e != cudaSuccess) { cleanup(); cudaGetLastError(); return fail(TN_ENOMEM, "gradient workspace"); }
+  // slab positions and maps, recovered from the host mesh tables
+  sz[0] = 0.0;
+  for (int q = 0; q < S; ++q) {
+    slog[q] = c->slab_log_host[q];
+    sz[q + 1] = c->slab_z_host[q + 1];
+  }
+  // adjoint: A lambda = g = sum_i w_i K_i u  (A is symmetric)
+  e = cudaMemcpyAsync(wdev, w_host, sizeof(double) * nl, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = tn_launch_energy_source(c->dm, u, wdev, g, s);
+  if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "adjoint source"); }
+  tn_solve_opts ao = *o;
+  ao.energy_rtol = 0.0;
+  st = solve_impl(c, &ao, g, lam, &r);
+  if (st != TN_OK && st != TN_ENOTCONV) { cleanup(); return st; }
+  tn_status result = st;
+  // slab boundary positions
+  dJ_dslab_z[0] = 0.0;
+  for (int b = 1; b <= S && e == cudaSuccess; ++b) {
+    slab_seed(hm, sz, slog, b, seed);
+    e = cudaMemcpyAsync(seed_dev, seed, sizeof(double) * (size_t)S * N, cudaMemcpyHostToDevice, s);
+    DevMesh m = c->dm;
+    m.d_slabdz = seed_dev;
+    const int a0 = b - 2 < 0 ? 0 : b - 2, a1 = b + 2 > S ? S : b + 2;
+    const int k0 = b - 1 < 0 ? 0 : b - 1, k1 = b + 1 > S ? S : b + 1;
+    if (e == cudaSuccess) e = tn_launch_apply_dual(m, a0, a1, u, lam, part, s);
+    const double dAu = e == cudaSuccess ? host_sum(part, (a1 - a0) * hm.ncol, tmp, s, &e) : 0.0;
+    if (e == cudaSuccess) e = tn_launch_energy_dual(m, k0, k1, u, wdev, part, s);
+    const double dK = e == cudaSuccess ? host_sum(part, (k1 - k0) * hm.ncol, tmp, s, &e) : 0.0;
+    dJ_dslab_z[b] = dK - dAu;
+  }
+  // moduli c11, c12, c44 of every layer
+  for (int L = 0; L < nl && e == cudaSuccess; ++L) {
+    int lo = S, hi = -1;
+    for (int q = 0; q < S; ++q)
+      if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+      dJ_dmat[3 * L + q] = 0.0;
+      if (hi < 0) continue;
+      for (int t = 0; t < 3 * nl; ++t) tmp[t] = (t == 3 * L + q) ? 1.0 : 0.0;
+      e = cudaMemcpyAsync(matseed, tmp, sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      DevMesh m = c->dm;
+      m.d_layer_c = matseed;
+      const int a0 = lo - 1 < 0 ? 0 : lo - 1, a1 = hi + 2 > S ? S : hi + 2;
+      if (e == cudaSuccess) e = tn_launch_apply_dual(m, a0, a1, u, lam, part, s);
+      const double dAu = e == cudaSuccess ? host_sum(part, (a1 - a0) * hm.ncol, tmp, s, &e) : 0.0;
+      if (e == cudaSuccess) e = tn_launch_energy_dual(m, lo, hi + 1, u, wdev, part, s);
+      const double dK = e == cudaSuccess ? host_sum(part, (hi + 1 - lo) * hm.ncol, tmp, s, &e) : 0.0;
+      dJ_dmat[3 * L + q] = dK - dAu;
+    }
+  }
+  // beam width: only the load depends on r0
+  if (e == cudaSuccess) e = tn_launch_rhs_dr0(c->dm, c->r0, c->F0, lam, part, 256, s);
+  if (e == cudaSuccess) *dJ_dr0 = host_sum(part, 256, tmp, s, &e);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "gradient contractions");
+  if (rep) *rep = r;
+  return result;
 }
 
 tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {

@@ -18,6 +18,7 @@
 // node forms its strain, stress, face terms and fluxes, and finally the
 // transposed derivative contractions give y.
 #include <cstdio>
+#include <type_traits>
 
 #include "tn_internal.h"
 
@@ -46,10 +47,33 @@ template <> struct Tab<double> {
   static __device__ __forceinline__ double D(int N, int a, int b) { return c_lgl.D[N][a * N + b]; }
   static __device__ __forceinline__ double w(int N, int a) { return c_lgl.w[N][a]; }
 };
+template <> struct Tab<Dual> {
+  static __device__ __forceinline__ double D(int N, int a, int b) { return c_lgl.D[N][a * N + b]; }
+  static __device__ __forceinline__ double w(int N, int a) { return c_lgl.w[N][a]; }
+};
 template <> struct Tab<float> {
   static __device__ __forceinline__ float D(int N, int a, int b) { return c_Df[N][a * N + b]; }
   static __device__ __forceinline__ float w(int N, int a) { return c_wf[N][a]; }
 };
+
+// geometry / material accessors: plain types round the FP64 tables, the dual
+// type also carries the derivative seed of the current direction
+template <typename T>
+__device__ __forceinline__ T slab_dz(const DevMesh &m, int s, int k) {
+  return (T)m.slabgeo[((size_t)s * SG_NF + SG_DZ) * m.N + k];
+}
+template <>
+__device__ __forceinline__ Dual slab_dz<Dual>(const DevMesh &m, int s, int k) {
+  return Dual(m.slabgeo[((size_t)s * SG_NF + SG_DZ) * m.N + k], m.d_slabdz ? m.d_slabdz[(size_t)s * m.N + k] : 0.0);
+}
+template <typename T>
+__device__ __forceinline__ T layer_coef(const DevMesh &m, int L, int q) {
+  return (T)m.layer_c[3 * L + q];
+}
+template <>
+__device__ __forceinline__ Dual layer_coef<Dual>(const DevMesh &m, int L, int q) {
+  return Dual(m.layer_c[3 * L + q], m.d_layer_c ? m.d_layer_c[3 * L + q] : 0.0);
+}
 
 // symmetric tensors as (xx, yy, zz, xy, xz, yz)
 template <typename T> struct Sym { T xx, yy, zz, xy, xz, yz; };
@@ -187,9 +211,12 @@ constexpr size_t apply_smem() {
   return sizeof(T) * (12 * N * N * N + 42 * N * N);
 }
 
-template <int N, typename T>
+// T = double / float: y = A u (and optionally partial[e] = u_e . y_e).
+// T = Dual: derivative of A u along the seeded direction; partial[e] = lam_e . (dA u)_e, y unused.
+template <int N, typename T, typename TIO>
 __global__ void __launch_bounds__(nthreads<N>())
-apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict__ y, double *__restrict__ partial,
+             const double *__restrict__ lam) {
   constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *su = reinterpret_cast<T *>(smem_raw);  // [3][n]
@@ -201,16 +228,16 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
   __shared__ T nbc[6][3];
   __shared__ double red[NT / 32];
 
-  const int e = blockIdx.x, tid = threadIdx.x;
+  const int e = e0 + blockIdx.x, tid = threadIdx.x;
   const int s = e / m.ncol, c = e - s * m.ncol;
-  const T *ue = u + (size_t)e * 3 * n;
-  for (int t = tid; t < 3 * n; t += NT) su[t] = ue[t];
+  const TIO *ue = u + (size_t)e * 3 * n;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = T(ue[t]);
   if (tid < 6) {
     face_info(m, s, c, fi, tid);
     const int L = m.slab_layer[fi.nbslab[tid]];
-    nbc[tid][0] = (T)m.layer_c[3 * L + 0];
-    nbc[tid][1] = (T)m.layer_c[3 * L + 1];
-    nbc[tid][2] = (T)m.layer_c[3 * L + 2];
+    nbc[tid][0] = layer_coef<T>(m, L, 0);
+    nbc[tid][1] = layer_coef<T>(m, L, 1);
+    nbc[tid][2] = layer_coef<T>(m, L, 2);
   }
   __syncthreads();
 
@@ -227,14 +254,14 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
       k2 = t2;
       if (d2 == 0) { i2 = end; j2 = a; } else { i2 = a; j2 = end; }
     }
-    const T *u2 = u + (size_t)fi.nb[f] * 3 * n;
+    const TIO *u2 = u + (size_t)fi.nb[f] * 3 * n;
     const int stride = d2 == 0 ? 1 : (d2 == 1 ? N : N2);
     const int base = (k2 * N + j2) * N + i2 - end * stride;
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       T line[N];
 #pragma unroll
-      for (int mm = 0; mm < N; ++mm) line[mm] = u2[cc * n + base + mm * stride];
+      for (int mm = 0; mm < N; ++mm) line[mm] = T(u2[cc * n + base + mm * stride]);
       T dn = T(0);
 #pragma unroll
       for (int mm = 0; mm < N; ++mm) dn += Tab<T>::D(N, end, mm) * line[mm];
@@ -243,7 +270,7 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
     }
     T h2;
     if (d2 == 2) {
-      h2 = T(2) * (T)m.slabgeo[((size_t)fi.nbslab[f] * SG_NF + SG_DZ) * N + end];
+      h2 = T(2) * slab_dz<T>(m, fi.nbslab[f], end);
     } else {
       const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
       const int q2 = j2 * N + i2;
@@ -256,9 +283,8 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
   __syncthreads();
 
   const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
-  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
   const int Lown = m.slab_layer[s];
-  const T c11 = (T)m.layer_c[3 * Lown], c12 = (T)m.layer_c[3 * Lown + 1], c44 = (T)m.layer_c[3 * Lown + 2];
+  const T c11 = layer_coef<T>(m, Lown, 0), c12 = layer_coef<T>(m, Lown, 1), c44 = layer_coef<T>(m, Lown, 2);
 
   // ---- neighbour traction n . Y_ext grad u_ext at the face nodes
   for (int t = tid; t < 6 * N2; t += NT) {
@@ -290,7 +316,7 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
       const int qq = j * N + i;
       jxx = (T)cg[CG_IXX * N2 + qq]; jxy = (T)cg[CG_IXY * N2 + qq];
       jex = (T)cg[CG_IEX * N2 + qq]; jey = (T)cg[CG_IEY * N2 + qq];
-      jdz = T(1) / (T)m.slabgeo[((size_t)fi.nbslab[f] * SG_NF + SG_DZ) * N + end2];
+      jdz = T(1) / slab_dz<T>(m, fi.nbslab[f], end2);
     } else {
       const T sg1 = fi.flip[f] ? T(-1) : T(1);
       const int a = fi.flip[f] ? N - 1 - t1 : t1;
@@ -308,7 +334,7 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
       const int q2 = j2 * N + i2;
       jxx = (T)g2[CG_IXX * N2 + q2]; jxy = (T)g2[CG_IXY * N2 + q2];
       jex = (T)g2[CG_IEX * N2 + q2]; jey = (T)g2[CG_IEY * N2 + q2];
-      jdz = T(1) / (T)sg[SG_DZ * N + t2];
+      jdz = T(1) / slab_dz<T>(m, s, t2);
     }
     const Sym<T> S2 = strain(dxi, deta, dzeta, jxx, jxy, jex, jey, jdz);
     const Sym<T> s2 = stress(S2, nbc[f][0], nbc[f][1], nbc[f][2]);
@@ -317,12 +343,14 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
     T nrm[3], W, h;
     face_geom<T, N>(f, i, j, k, (T)cg[CG_IXX * N2 + qq], (T)cg[CG_IXY * N2 + qq],
                     (T)cg[CG_IEX * N2 + qq], (T)cg[CG_IEY * N2 + qq], (T)cg[CG_DET * N2 + qq],
-                    (T)sg[SG_DZ * N + k], nrm, W, h);
+                    slab_dz<T>(m, s, k), nrm, W, h);
     T tr[3];
     contract_n(s2, nrm, tr);
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) nbt[(f * 3 + cc) * N2 + q] = tr[cc];
   }
+
+  __syncthreads();
 
   // ---- per node: strain, stress, face terms, fluxes
   T ysurf[3] = {T(0), T(0), T(0)};
@@ -346,7 +374,7 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
     const int qq = j * N + i;
     const T ixx = (T)cg[CG_IXX * N2 + qq], ixy = (T)cg[CG_IXY * N2 + qq];
     const T iex = (T)cg[CG_IEX * N2 + qq], iey = (T)cg[CG_IEY * N2 + qq];
-    const T det2 = (T)cg[CG_DET * N2 + qq], dz = (T)sg[SG_DZ * N + k];
+    const T det2 = (T)cg[CG_DET * N2 + qq], dz = slab_dz<T>(m, s, k);
     const T idz = T(1) / dz;
     const Sym<T> S = strain(dxi, deta, dzeta, ixx, ixy, iex, iey, idz);
     const T wJ = Tab<T>::w(N, i) * Tab<T>::w(N, j) * Tab<T>::w(N, k) * det2 * dz;
@@ -414,7 +442,6 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
   // ---- weak divergence: y = sum_m D_m^T F^m
   double dot = 0.0;
   if (active) {
-    T *ye = y + (size_t)e * 3 * n;
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       const T *F0 = sF + (0 * 3 + cc) * n, *F1 = sF + (1 * 3 + cc) * n, *F2 = sF + (2 * 3 + cc) * n;
@@ -425,8 +452,12 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
         acc += Tab<T>::D(N, mm, j) * F1[(k * N + mm) * N + i];
         acc += Tab<T>::D(N, mm, k) * F2[(mm * N + j) * N + i];
       }
-      ye[cc * n + p] = acc;
-      dot += (double)acc * (double)su[cc * n + p];
+      if constexpr (std::is_same<T, Dual>::value) {
+        dot += acc.d * lam[(size_t)e * 3 * n + cc * n + p];
+      } else {
+        y[(size_t)e * 3 * n + cc * n + p] = acc;
+        dot += (double)acc * (double)su[cc * n + p];
+      }
     }
   }
   if (partial) {
@@ -437,23 +468,33 @@ apply_kernel(const DevMesh m, const T *__restrict__ u, T *__restrict__ y, double
     if (tid == 0) {
       double sum = 0.0;
       for (int w = 0; w < NT / 32; ++w) sum += red[w];
-      partial[e] = sum;
+      partial[blockIdx.x] = sum;
     }
   }
 }
 
-template <int N, typename T>
-cudaError_t launch_apply_n(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+template <int N, typename T, typename TIO>
+cudaError_t launch_apply_range(const DevMesh &m, int s0, int s1, const TIO *u, TIO *y, double *partial,
+                               const double *lam, cudaStream_t st) {
   constexpr size_t sm = apply_smem<N, T>();
-  static bool configured = false;  // per process; attribute is per function
-  if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T>,
+  static int configured_device = -1;  // the attribute is per function and device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t err = cudaFuncSetAttribute(apply_kernel<N, T, TIO>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
-    configured = true;
+    configured_device = dev;
   }
-  apply_kernel<N, T><<<m.E, nthreads<N>(), sm, st>>>(m, u, y, partial);
+  const int nblk = (s1 - s0) * m.ncol;
+  if (nblk <= 0) return cudaSuccess;
+  apply_kernel<N, T, TIO><<<nblk, nthreads<N>(), sm, st>>>(m, s0 * m.ncol, u, y, partial, lam);
   return cudaGetLastError();
+}
+
+template <int N, typename T>
+cudaError_t launch_apply_n(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+  return launch_apply_range<N, T, T>(m, 0, m.nslab, u, y, partial, nullptr, st);
 }
 
 template <typename T>
@@ -599,24 +640,81 @@ __global__ void diag_kernel(const DevMesh m, double *__restrict__ dg) {
 }
 
 // ------------------------------------------------------------- energies
-// elem[e] = 1/2 sum_p w_p detJ_p S_p : Y : S_p, S = sym grad u (unlifted)
-template <int N>
+// elem[blockIdx.x] = 1/2 sum_p w_p detJ_p S_p : Y : S_p, S = sym grad u
+// (unlifted), for the elements e0 + blockIdx.x; T = Dual gives the derivative
+// along the seeded direction instead; scaled by w[layer] if w is given.
+template <int N, typename T>
 __global__ void __launch_bounds__(nthreads<N>())
-energy_kernel(const DevMesh m, const double *__restrict__ u, double *__restrict__ elem) {
+energy_kernel(const DevMesh m, int e0, const double *__restrict__ u, const double *__restrict__ w,
+              double *__restrict__ elem) {
   constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
   __shared__ double su[3 * n];
   __shared__ double red[NT / 32];
+  const int e = e0 + blockIdx.x, tid = threadIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = u[(size_t)e * 3 * n + t];
+  __syncthreads();
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const int L = m.slab_layer[s];
+  const T c11 = layer_coef<T>(m, L, 0), c12 = layer_coef<T>(m, L, 1), c44 = layer_coef<T>(m, L, 2);
+  double en = 0.0;
+  if (tid < n) {
+    const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
+    T dxi[3], deta[3], dzeta[3];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double *v = su + cc * n;
+      double a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a0 += Tab<double>::D(N, i, mm) * v[(k * N + j) * N + mm];
+        a1 += Tab<double>::D(N, j, mm) * v[(k * N + mm) * N + i];
+        a2 += Tab<double>::D(N, k, mm) * v[(mm * N + j) * N + i];
+      }
+      dxi[cc] = T(a0); deta[cc] = T(a1); dzeta[cc] = T(a2);
+    }
+    const int q = j * N + i;
+    const T dz = slab_dz<T>(m, s, k);
+    const Sym<T> S = strain<T>(dxi, deta, dzeta, T(cg[CG_IXX * N2 + q]), T(cg[CG_IXY * N2 + q]),
+                               T(cg[CG_IEX * N2 + q]), T(cg[CG_IEY * N2 + q]), T(1.0) / dz);
+    const Sym<T> sg2 = stress(S, c11, c12, c44);
+    const T dens = S.xx * sg2.xx + S.yy * sg2.yy + S.zz * sg2.zz +
+                   T(2.0) * (S.xy * sg2.xy + S.xz * sg2.xz + S.yz * sg2.yz);
+    const T val = T(0.5 * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) *
+                    cg[CG_DET * N2 + q]) * dz * dens;
+    if constexpr (std::is_same<T, Dual>::value) en = val.d;
+    else en = val;
+    if (w) en *= w[L];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
+  if ((tid & 31) == 0) red[tid >> 5] = en;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int ww = 0; ww < NT / 32; ++ww) sum += red[ww];
+    elem[blockIdx.x] = sum;
+  }
+}
+
+// g_e = w[layer(e)] K_e u: the weak divergence of w detJ Y : sym grad u
+// (the volume part of the operator, no faces) -- d(sum_i w_i U_i)/du
+template <int N>
+__global__ void __launch_bounds__(nthreads<N>())
+energy_source_kernel(const DevMesh m, const double *__restrict__ u, const double *__restrict__ w,
+                     double *__restrict__ g) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  __shared__ double su[3 * n];
+  __shared__ double sF[9 * n];
   const int e = blockIdx.x, tid = threadIdx.x;
   const int s = e / m.ncol, c = e - s * m.ncol;
   for (int t = tid; t < 3 * n; t += NT) su[t] = u[(size_t)e * 3 * n + t];
   __syncthreads();
   const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
-  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
   const int L = m.slab_layer[s];
   const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
-  double en = 0.0;
+  const double wl = w[L];
+  const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
   if (tid < n) {
-    const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
     double dxi[3], deta[3], dzeta[3];
     for (int cc = 0; cc < 3; ++cc) {
       const double *v = su + cc * n;
@@ -630,23 +728,65 @@ energy_kernel(const DevMesh m, const double *__restrict__ u, double *__restrict_
       dxi[cc] = a0; deta[cc] = a1; dzeta[cc] = a2;
     }
     const int q = j * N + i;
-    const double dz = sg[SG_DZ * N + k];
-    const Sym<double> S = strain(dxi, deta, dzeta, cg[CG_IXX * N2 + q], cg[CG_IXY * N2 + q],
-                                 cg[CG_IEX * N2 + q], cg[CG_IEY * N2 + q], 1.0 / dz);
-    const Sym<double> sg2 = stress(S, c11, c12, c44);
-    const double dens = S.xx * sg2.xx + S.yy * sg2.yy + S.zz * sg2.zz +
-                        2.0 * (S.xy * sg2.xy + S.xz * sg2.xz + S.yz * sg2.yz);
-    en = 0.5 * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) *
-         cg[CG_DET * N2 + q] * dz * dens;
+    const double ixx = cg[CG_IXX * N2 + q], ixy = cg[CG_IXY * N2 + q];
+    const double iex = cg[CG_IEX * N2 + q], iey = cg[CG_IEY * N2 + q];
+    const double dz = m.slabgeo[((size_t)s * SG_NF + SG_DZ) * N + k], idz = 1.0 / dz;
+    const Sym<double> S = strain<double>(dxi, deta, dzeta, ixx, ixy, iex, iey, idz);
+    const double wJ = wl * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) *
+                      cg[CG_DET * N2 + q] * dz;
+    const Sym<double> Se = {wJ * S.xx, wJ * S.yy, wJ * S.zz, wJ * S.xy, wJ * S.xz, wJ * S.yz};
+    const Sym<double> se = stress(Se, c11, c12, c44);
+    sF[0 * n + p] = ixx * se.xx + ixy * se.xy;
+    sF[1 * n + p] = ixx * se.xy + ixy * se.yy;
+    sF[2 * n + p] = ixx * se.xz + ixy * se.yz;
+    sF[3 * n + p] = iex * se.xx + iey * se.xy;
+    sF[4 * n + p] = iex * se.xy + iey * se.yy;
+    sF[5 * n + p] = iex * se.xz + iey * se.yz;
+    sF[6 * n + p] = idz * se.xz;
+    sF[7 * n + p] = idz * se.yz;
+    sF[8 * n + p] = idz * se.zz;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
-  if ((tid & 31) == 0) red[tid >> 5] = en;
   __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < NT / 32; ++w) sum += red[w];
-    elem[e] = sum;
+  if (tid < n) {
+    for (int cc = 0; cc < 3; ++cc) {
+      const double *F0 = sF + cc * n, *F1 = sF + (3 + cc) * n, *F2 = sF + (6 + cc) * n;
+      double acc = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        acc += Tab<double>::D(N, mm, i) * F0[(k * N + j) * N + mm];
+        acc += Tab<double>::D(N, mm, j) * F1[(k * N + mm) * N + i];
+        acc += Tab<double>::D(N, mm, k) * F2[(mm * N + j) * N + i];
+      }
+      g[(size_t)e * 3 * n + cc * n + p] = acc;
+    }
+  }
+}
+
+// partial sums of lam . db/dr0 over the top-surface nodes:
+// b_z = -W F0 exp(-r^2/r0^2) / (pi r0^2),  db_z/dr0 = b_z (2 r^2 / r0^3 - 2 / r0)
+__global__ void rhs_dr0_kernel(const DevMesh m, double r0, double F0, const double *__restrict__ lam,
+                               double *__restrict__ part) {
+  const int N = m.N, n = N * N * N, N2 = N * N;
+  const size_t total = (size_t)m.ncol * N2;  // top-surface nodes
+  const double norm = F0 / (M_PI * r0 * r0), ir2 = 1.0 / (r0 * r0);
+  double acc = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int e = (int)(t / N2), q = (int)(t % N2), i = q % N, j = q / N;
+    const double *g = m.colgeo + (size_t)e * CG_NF * N2;
+    const double X = g[CG_X * N2 + q], Y = g[CG_Y * N2 + q], r2 = X * X + Y * Y;
+    const double W = c_lgl.w[N][i] * c_lgl.w[N][j] * g[CG_DET * N2 + q];
+    const double bz = -W * norm * exp(-r2 * ir2);
+    const double dbz = bz * (2.0 * r2 * ir2 / r0 - 2.0 / r0);
+    acc += lam[((size_t)e * 3 + 2) * n + (N - 1) * N2 + q] * dbz;
+  }
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
   }
 }
 
@@ -674,7 +814,16 @@ __global__ void layer_sum_kernel(const DevMesh m, const double *__restrict__ ele
 
 template <int N>
 cudaError_t launch_energy_n(const DevMesh &m, const double *u, double *elem, cudaStream_t st) {
-  energy_kernel<N><<<m.E, nthreads<N>(), 0, st>>>(m, u, elem);
+  energy_kernel<N, double><<<m.E, nthreads<N>(), 0, st>>>(m, 0, u, nullptr, elem);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_energy_dual_n(const DevMesh &m, int s0, int s1, const double *u, const double *w,
+                                 double *epart, cudaStream_t st) {
+  const int nblk = (s1 - s0) * m.ncol;
+  if (nblk <= 0) return cudaSuccess;
+  energy_kernel<N, Dual><<<nblk, nthreads<N>(), 0, st>>>(m, s0 * m.ncol, u, w, epart);
   return cudaGetLastError();
 }
 
@@ -713,5 +862,38 @@ cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem, do
   }
   if (err != cudaSuccess) return err;
   layer_sum_kernel<<<1, 256, 0, st>>>(m, elem, layer);
+  return cudaGetLastError();
+}
+
+#define TN_DISPATCH_N(...)                  \
+  switch (m.N) {                            \
+    case 3: { constexpr int NN = 3; __VA_ARGS__; } \
+    case 4: { constexpr int NN = 4; __VA_ARGS__; } \
+    case 5: { constexpr int NN = 5; __VA_ARGS__; } \
+    case 6: { constexpr int NN = 6; __VA_ARGS__; } \
+    case 7: { constexpr int NN = 7; __VA_ARGS__; } \
+    case 8: { constexpr int NN = 8; __VA_ARGS__; } \
+    case 9: { constexpr int NN = 9; __VA_ARGS__; } \
+    default: return cudaErrorInvalidValue;  \
+  }
+
+cudaError_t tn_launch_apply_dual(const DevMesh &m, int s0, int s1, const double *u, const double *lam,
+                                 double *part, cudaStream_t st) {
+  TN_DISPATCH_N(return launch_apply_range<NN, Dual, double>(m, s0, s1, u, nullptr, part, lam, st))
+}
+
+cudaError_t tn_launch_energy_dual(const DevMesh &m, int s0, int s1, const double *u, const double *w,
+                                  double *epart, cudaStream_t st) {
+  TN_DISPATCH_N(return launch_energy_dual_n<NN>(m, s0, s1, u, w, epart, st))
+}
+
+cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const double *w, double *g,
+                                    cudaStream_t st) {
+  TN_DISPATCH_N(energy_source_kernel<NN><<<m.E, nthreads<NN>(), 0, st>>>(m, u, w, g); return cudaGetLastError())
+}
+
+cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const double *lam, double *part,
+                              int nparts, cudaStream_t st) {
+  rhs_dr0_kernel<<<nparts, 256, 0, st>>>(m, r0, F0, lam, part);
   return cudaGetLastError();
 }

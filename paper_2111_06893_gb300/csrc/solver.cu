@@ -415,6 +415,8 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
   cudaError_t err = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   TN_CU(err);
+  double best = INFINITY;
+  int stall = 0;
   for (;;) {
     g_launches += (zl ? 6LL : 5LL) * chunk;
     err = cudaGraphLaunch(exec, st);
@@ -425,6 +427,9 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     if (err != cudaSuccess) break;
     if (s_host->done) break;
     if (hook.fn && hook.fn(hook.user)) break;
+    // stagnation: the recursive residual has not halved for 40 chunks
+    if (s_host->rr < 0.5 * best) { best = s_host->rr; stall = 0; }
+    else if (++stall >= 40) break;
   }
   cudaGraphExecDestroy(exec);
   *applies += s_host->iters;

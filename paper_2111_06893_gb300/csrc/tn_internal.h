@@ -45,7 +45,33 @@ struct DevMesh {
   const int *colnbf;      // [ncol][4]: neighbour face (0..3) | (flip << 2)
   const int *slab_layer;  // [nslab]
   const double *layer_c;  // [n_layers][3]: c11, c12, c44 (isotropic: lambda+2mu, lambda, mu)
+  // forward-mode seeds for derivative kernels (nullptr: no dependence)
+  const double *d_slabdz = nullptr;  // [nslab][N]: d(dz/dzeta)/dtheta at each node
+  const double *d_layer_c = nullptr;  // [n_layers][3]: d(c11, c12, c44)/dtheta
 };
+
+// forward-mode dual number (value, derivative along one direction)
+struct Dual {
+  double v, d;
+  Dual() = default;
+  __host__ __device__ constexpr Dual(double a) : v(a), d(0.0) {}
+  __host__ __device__ constexpr Dual(double a, double b) : v(a), d(b) {}
+};
+__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__host__ __device__ inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__host__ __device__ inline Dual operator/(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+__host__ __device__ inline Dual &operator+=(Dual &a, Dual b) { a = a + b; return a; }
+__host__ __device__ inline Dual &operator-=(Dual &a, Dual b) { a = a - b; return a; }
+__host__ __device__ inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+__device__ inline Dual sqrt(Dual a) {
+  const double r = ::sqrt(a.v);
+  return Dual(r, 0.5 * a.d / r);
+}
 
 // LGL tables in constant memory, indexed by N (filled at context creation)
 struct LglTables {
@@ -72,6 +98,19 @@ void free_host_mesh(HostMesh *m);
 
 // kernels (kernels.cu) -- launchers return cudaError_t of the launch
 cudaError_t tn_upload_lgl(const LglTables *t);
+// derivative kernels: over the elements of slabs [s0, s1),
+//   part[e - s0*ncol] = lam_e . (dA/dtheta u)_e        (seeds in m.d_*)
+//   epart[e - s0*ncol] = w[layer(e)] dU_e/dtheta|_u
+cudaError_t tn_launch_apply_dual(const DevMesh &m, int s0, int s1, const double *u, const double *lam,
+                                 double *part, cudaStream_t st);
+cudaError_t tn_launch_energy_dual(const DevMesh &m, int s0, int s1, const double *u, const double *w,
+                                  double *epart, cudaStream_t st);
+// g = sum_i w_i K_i u (the derivative of sum_i w_i U_i with respect to u)
+cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const double *w, double *g,
+                                    cudaStream_t st);
+// part[b] = partial sums of lam . db/dr0 (beam width derivative of the load)
+cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const double *lam, double *part,
+                              int nparts, cudaStream_t st);
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
                             double *partial, const void *dotwith, cudaStream_t st);
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st);

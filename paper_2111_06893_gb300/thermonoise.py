@@ -28,7 +28,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 # every entry point declared in include/thermonoise.h
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
-           "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply"]
+           "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad"]
 
 
 class MeshDesc(C.Structure):
@@ -95,6 +95,8 @@ def load():
         "tn_layer_energies": (C.c_int, [vp, vp, dp]),
         "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
+        "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
+                                     C.POINTER(SolveReport)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +244,40 @@ class Context:
                                        C.c_void_p(z.data_ptr())))
         return z
 
+    @staticmethod
+    def _opts(mode, rtol, inner_rtol, max_iter, max_outer, check_every, precond, energy_rtol):
+        o = SolveOpts()
+        o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
+        o.precond = PRECONDS[precond]
+        o.rtol, o.inner_rtol = rtol, inner_rtol
+        o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
+        o.energy_rtol = energy_rtol
+        o.use_x0 = 0
+        return o
+
+    def energy_grad(self, u, w, mode="f64", rtol=1e-12, inner_rtol=0.05, max_iter=200000, max_outer=60,
+                    check_every=25, precond="zline", raise_on_error=True):
+        """Adjoint gradient of J = sum_i w_i U_i at the solution u: returns
+        dJ/dslab_z (n_slabs + 1), dJ/dr0, dJ/d(c11, c12, c44) per layer."""
+        self._check_tensor(u, self._torch.float64, "u")
+        nl = len(self.desc["materials"])
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (nl,):
+            raise ValueError(f"w needs {nl} values")
+        ns = len(self.desc["slab_z"]) - 1
+        gz = np.zeros(ns + 1)
+        gr = np.zeros(1)
+        gm = np.zeros(3 * nl)
+        o = self._opts(mode, rtol, inner_rtol, max_iter, max_outer, check_every, precond, 0.0)
+        rep = SolveReport()
+        dp = C.POINTER(C.c_double)
+        st = load().tn_energy_grad(self._h, C.byref(o), C.c_void_p(u.data_ptr()), w.ctypes.data_as(dp), None,
+                                   gz.ctypes.data_as(dp), gr.ctypes.data_as(dp), gm.ctypes.data_as(dp),
+                                   C.byref(rep))
+        if raise_on_error:
+            _check(st)
+        return {"slab_z": gz, "r0": float(gr[0]), "moduli": gm.reshape(nl, 3), "report": rep.as_dict()}
+
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=0.05, max_iter=200000, max_outer=60,
               x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",
               energy_rtol=0.0):
@@ -290,3 +326,59 @@ def setup(desc, device=0, stream=None):
     ctx.set_materials(desc["materials"])
     ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
     return ctx
+
+
+def iso_moduli(Y, nu):
+    """(c11, c12, c44) = (lambda + 2 mu, lambda, mu) from Young's modulus and
+    Poisson ratio (the footnote to Eq. (constrel_iso)); works on floats and on
+    torch tensors (differentiably)."""
+    mu = Y / (2.0 * (1.0 + nu))
+    lam = Y * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    return lam + 2.0 * mu, lam, mu
+
+
+def _energy_fn_class():
+    import torch
+
+    class EnergyFn(torch.autograd.Function):
+        """U = EnergyFn.apply(slab_z, r0, moduli, desc, solve_kw): per-layer
+        energies of the mirror `desc` with slab boundary positions slab_z
+        (n_slabs + 1, slab_z[0] = 0), beam width r0 and moduli
+        [n_layers, 3] = (c11, c12, c44); backward runs the adjoint
+        (tn_energy_grad), which reuses the forward operator."""
+
+        @staticmethod
+        def forward(ctx, slab_z, r0, moduli, desc, solve_kw):
+            d = dict(desc)
+            d["slab_z"] = [float(v) for v in slab_z.detach().cpu().tolist()]
+            d["beam"] = {"r0": float(r0.detach()), "F0": desc["beam"]["F0"]}
+            mats = [{"kind": "cubic", "c11": float(c[0]), "c12": float(c[1]), "c44": float(c[2])}
+                    for c in moduli.detach().cpu().tolist()]
+            d["materials"] = mats
+            tc = setup(d)
+            kw = dict(solve_kw or {})
+            u, _ = tc.solve(**kw)
+            U = tc.layer_energies(u)
+            ctx.tc, ctx.u, ctx.kw = tc, u, kw
+            return torch.tensor(U, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gU):
+            kw = {k: v for k, v in ctx.kw.items() if k in ("mode", "rtol", "inner_rtol", "precond",
+                                                         "max_iter", "max_outer", "check_every")}
+            g = ctx.tc.energy_grad(ctx.u, gU.detach().cpu().numpy(), **kw)
+            return (torch.tensor(g["slab_z"], dtype=torch.float64), torch.tensor(g["r0"], dtype=torch.float64),
+                    torch.tensor(g["moduli"], dtype=torch.float64), None, None)
+
+    return EnergyFn
+
+
+_ENERGY_FN = None
+
+
+def energy_fn():
+    """The torch.autograd.Function computing per-layer energies (see above)."""
+    global _ENERGY_FN
+    if _ENERGY_FN is None:
+        _ENERGY_FN = _energy_fn_class()
+    return _ENERGY_FN

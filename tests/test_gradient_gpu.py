@@ -1,0 +1,102 @@
+"""Adjoint energy gradients on the GPU against the oracle's complex-step
+gradients (exact derivatives of the discrete energies) and against central
+finite differences of GPU solves."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import gradient as G
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_06893_gb300 import build
+    build.build()
+
+
+def layered_box():
+    return W.box([-1.0, 0.2, 1.0], [-0.5, 1.0], [0.0, -0.3, -0.8, -1.3], 3, None, slab_layer=[0, 1, 2],
+                 materials=[W.CRYSTAL_A, W.COATING_HIGH, W.FUSED_SILICA], penalty_C=3.0,
+                 bc_side="fixed", bc_bottom="fixed", r0=0.7)
+
+
+def thin_cylinder():
+    return W.cylinder(10.0, 10.0, [0.02, 0.05], [W.CRYSTAL_B, W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 2,
+                      r0=1.3)
+
+
+def iso_chain(m):
+    """d(c11, c12, c44)/d(Y, nu) for an isotropic material."""
+    Y, nu = m["Y"], m["nu"]
+    h = 1e-7
+    from paper_2111_06893_gb300.thermonoise import iso_moduli
+    base = np.array(iso_moduli(Y, nu))
+    dY = (np.array(iso_moduli(Y * (1 + h), nu)) - np.array(iso_moduli(Y * (1 - h), nu))) / (2 * h * Y)
+    dn = (np.array(iso_moduli(Y, nu + h)) - np.array(iso_moduli(Y, nu - h))) / (2 * h)
+    return base, dY, dn
+
+
+@pytest.mark.parametrize("make", [layered_box, thin_cylinder])
+def test_adjoint_gradient_matches_oracle_complex_step(make):
+    from paper_2111_06893_gb300 import thermonoise
+    desc = make()
+    ctx = thermonoise.setup(desc)
+    u, _ = ctx.solve(mode="f64", rtol=1e-13, energy_rtol=1e-14)
+    nl = len(desc["materials"])
+    rng = np.random.default_rng(4)
+    w = rng.uniform(0.5, 2.0, size=nl)
+    g = ctx.energy_grad(u, w, mode="f64", rtol=1e-13)
+    ns = len(desc["slab_z"]) - 1
+    # slab boundaries
+    for s in range(1, ns + 1):
+        ref = float(np.dot(w, G.energy_derivative(desc, ("slab_z", s))))
+        scale = max(abs(ref), 1e-3 * max(abs(v) for v in g["slab_z"]))
+        assert abs(g["slab_z"][s] - ref) <= 1e-8 * scale, ("slab_z", s, g["slab_z"][s], ref)
+    ref = float(np.dot(w, G.energy_derivative(desc, ("r0",))))
+    assert abs(g["r0"] - ref) <= 1e-8 * abs(ref), ("r0", g["r0"], ref)
+    # moduli: cubic layers directly, isotropic through (Y, nu)
+    for L, m in enumerate(desc["materials"]):
+        if m["kind"] == "cubic":
+            for q, key in enumerate(["c11", "c12", "c44"]):
+                ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
+                assert abs(g["moduli"][L, q] - ref) <= 1e-8 * abs(ref), (L, key, g["moduli"][L, q], ref)
+        else:
+            _, dY, dn = iso_chain(m)
+            for key, dc in (("Y", dY), ("nu", dn)):
+                ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
+                got = float(np.dot(g["moduli"][L], dc))
+                assert abs(got - ref) <= 1e-6 * abs(ref), (L, key, got, ref)
+
+
+def test_gradient_matches_gpu_finite_differences_and_autograd():
+    from paper_2111_06893_gb300 import thermonoise
+    desc = thin_cylinder()
+    EnergyFn = thermonoise.energy_fn()
+    slab_z = torch.tensor(desc["slab_z"], dtype=torch.float64, requires_grad=True)
+    r0 = torch.tensor(desc["beam"]["r0"], dtype=torch.float64, requires_grad=True)
+    mod = torch.tensor([thermonoise.iso_moduli(m["Y"], m["nu"]) if m["kind"] == "iso"
+                        else (m["c11"], m["c12"], m["c44"]) for m in desc["materials"]],
+                       dtype=torch.float64, requires_grad=True)
+    kw = {"mode": "f64", "rtol": 1e-13, "energy_rtol": 1e-14}
+    U = EnergyFn.apply(slab_z, r0, mod, desc, kw)
+    J = U[0] * 2.0 + U[1] + 0.5 * U[-1]
+    J.backward()
+
+    def Jval(sz, rr):
+        with torch.no_grad():
+            V = EnergyFn.apply(sz, rr, mod, desc, kw)
+        return float(V[0] * 2.0 + V[1] + 0.5 * V[-1])
+
+    # thickness of the first coating layer: moves slab_z[1:] ... only slab_z[1] here
+    h = 1e-6
+    e1 = torch.zeros_like(slab_z)
+    e1[1] = h
+    fd = (Jval(slab_z.detach() + e1, r0.detach()) - Jval(slab_z.detach() - e1, r0.detach())) / (2 * h)
+    assert abs(slab_z.grad[1].item() - fd) <= 1e-5 * abs(fd), (slab_z.grad[1].item(), fd)
+    fd = (Jval(slab_z.detach(), r0.detach() + h) - Jval(slab_z.detach(), r0.detach() - h)) / (2 * h)
+    assert abs(r0.grad.item() - fd) <= 1e-5 * abs(fd), (r0.grad.item(), fd)

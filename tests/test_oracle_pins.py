@@ -358,3 +358,27 @@ def test_noise_psd_independent_of_force_and_levin_half_space():
     Sq = ob.noise_psd([ob.half_space_energy(Y, nu, 1.0, r0)], [phi], kT, f, 1.0)
     levin = 2 * kT * (1 - nu ** 2) * phi / (math.pi ** 1.5 * f * math.sqrt(2) * r0 * Y)
     assert abs(Sq / levin - 1) < 1e-13
+
+
+def test_split_jacobian_matches_full_complex_step():
+    """The geometry's Jacobian (complex step of the cross-section map, closed
+    form dZ/dzeta) equals the full 3-D complex-step Jacobian of the map."""
+    m = Mesh(W.cylinder(10.0, 10.0, [0.05, 0.3], [W.COATING_HIGH, W.FUSED_SILICA], W.FUSED_SILICA,
+                        2, 4, 3))
+    rng = np.random.default_rng(5)
+    for e in [0, 7, 40, m.E - 1]:
+        xi = rng.uniform(-1, 1, size=(6, 3))
+        assert np.allclose(m.jacobian_split(e, xi), m.jacobian(e, xi), rtol=1e-13, atol=1e-13)
+
+
+def test_complex_step_energy_gradients_match_central_differences():
+    """The oracle's reference gradients (complex step through mesh, operator,
+    solve and energies) against central finite differences of full solves."""
+    from oracle import gradient as G
+    d = W.box([-1.0, 0.2], [-0.5, 1.0], [0.0, -0.3, -1.3], 2, None, slab_layer=[0, 1],
+              materials=[W.CRYSTAL_A, W.FUSED_SILICA], penalty_C=3.0, bc_side="fixed", bc_bottom="fixed")
+    for p, h, tol in [(("slab_z", 1), 1e-6, 1e-7), (("r0",), 1e-6, 1e-8),
+                      (("material", 0, "c11"), 1e-6 * 119.9e9, 1e-6), (("material", 1, "nu"), 1e-6, 1e-5)]:
+        cs = G.energy_derivative(d, p)
+        fd = np.real(G.energies(G.perturbed(d, p, h)) - G.energies(G.perturbed(d, p, -h))) / (2 * h)
+        assert np.max(np.abs(cs - fd)) <= tol * np.max(np.abs(cs)), (p, cs, fd)
