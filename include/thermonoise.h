@@ -154,8 +154,11 @@ tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *
  * precond: TN_PC_JACOBI or TN_PC_ZLINE (see tn_precond_apply).
  * mode TN_SOLVE_F64: preconditioned CG in FP64, restarted from the current
  * iterate (true residual) if the recursive residual drifted.
- * mode TN_SOLVE_MIXED_F32: iterative refinement, FP64 residual b - A x and
- * update, inner Jacobi-PCG entirely in FP32 to inner_rtol.
+ * mode TN_SOLVE_MIXED_F32: flexible CG in FP64 (residual, update and a window
+ * of fcg_window previous directions kept A-orthogonal) preconditioned by an
+ * inner PCG entirely in FP32 (vectors, operator, preconditioner), run to
+ * inner_rtol or inner_max iterations on the normalised FP64 residual;
+ * max_outer bounds the FP64 steps.
  * Stops when ||b - A u||_2 <= rtol ||b||_2 (FP64 residual), or by the energy
  * test of energy_rtol, or when the FP64 residual stagnates (thin layers put
  * its rounding floor near eps64 * cond(A)); u_dev holds the
@@ -171,6 +174,8 @@ typedef struct {
   int max_outer;
   int use_x0;
   int check_every;          /* iterations between host convergence checks */
+  int inner_max;            /* mixed: FP32 PCG iterations per outer step (0: 30) */
+  int fcg_window;           /* mixed: directions kept by the flexible CG (0: 8, max 16) */
   double energy_rtol;       /* > 0: also stop once every layer energy U_i
                                changes by <= energy_rtol (relative) between
                                two checks (refinement steps, or check_every

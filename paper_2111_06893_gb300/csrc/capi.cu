@@ -52,6 +52,7 @@ struct tn_ctx {
   DevMesh dm{};
   double *d_colgeo = nullptr, *d_slabgeo = nullptr, *d_layer_c = nullptr;
   int *d_colnb = nullptr, *d_colnbf = nullptr, *d_slab_layer = nullptr;
+  float *d_colgeo32 = nullptr, *d_slabgeo32 = nullptr, *d_layer_c32 = nullptr;
   double *slab_z_host = nullptr;
   int *slab_log_host = nullptr;
   double r0 = 1.0, F0 = 1.0;
@@ -65,6 +66,13 @@ struct tn_ctx {
   double *part_elem = nullptr, *part_red = nullptr, *sum_dev = nullptr;
   tn_pcg_scalars *scal = nullptr, *scal_host = nullptr;
   double *elem_energy = nullptr, *layer_energy = nullptr;
+  // flexible-CG window (mixed mode)
+  double *fcg = nullptr;
+  const double **fcg_ptrs = nullptr;   // device: [16] P, [16] AP, [2] pair
+  double *fcg_beta = nullptr;
+  double *fcg_part = nullptr;
+  double *fcg_host = nullptr;          // host tmp for partial sums
+  int fcg_m = 0;
   size_t ws_E = 0;
   int ws_layers = 0;
   // z-line preconditioner (valid while mesh and materials are unchanged)
@@ -90,6 +98,8 @@ static void free_mesh(tn_ctx *c) {
   dfree(c->d_colnb);
   dfree(c->d_colnbf);
   dfree(c->d_slab_layer);
+  dfree(c->d_colgeo32);
+  dfree(c->d_slabgeo32);
   tn::free_host_mesh(&c->hm);
   std::free(c->slab_z_host);
   std::free(c->slab_log_host);
@@ -104,6 +114,10 @@ static void free_ws(tn_ctx *c) {
   dfree(c->q32); dfree(c->d32);
   dfree(c->part_elem); dfree(c->part_red); dfree(c->sum_dev); dfree(c->scal);
   dfree(c->elem_energy); dfree(c->layer_energy);
+  dfree(c->fcg); dfree(c->fcg_ptrs); dfree(c->fcg_beta); dfree(c->fcg_part);
+  std::free(c->fcg_host);
+  c->fcg_host = nullptr;
+  c->fcg_m = 0;
   if (c->scal_host) cudaFreeHost(c->scal_host);
   c->scal_host = nullptr;
   c->ws_ndof = 0;
@@ -137,6 +151,34 @@ static tn_status ensure_ws(tn_ctx *c) {
   c->ws_ndof = n;
   c->ws_E = c->dm.E;
   c->ws_layers = c->dm.n_layers;
+  return TN_OK;
+}
+
+static tn_status ensure_fcg(tn_ctx *c, int m) {
+  if (c->fcg_m == m) return TN_OK;
+  dfree(c->fcg); dfree(c->fcg_ptrs); dfree(c->fcg_beta); dfree(c->fcg_part);
+  std::free(c->fcg_host);
+  c->fcg_host = nullptr;
+  c->fcg_m = 0;
+  const size_t n = c->ndof;
+  const int nb = tn::reduction_blocks();
+  cudaError_t e = cudaMalloc((void **)&c->fcg, sizeof(double) * n * 2 * m);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->fcg_ptrs, sizeof(double *) * 34);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->fcg_beta, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->fcg_part, sizeof(double) * 16 * nb);
+  c->fcg_host = (double *)std::malloc(sizeof(double) * 16 * nb);
+  if (e != cudaSuccess || !c->fcg_host) {
+    cudaGetLastError();
+    return fail(TN_ENOMEM, "flexible CG window of %d directions", m);
+  }
+  const double *ptrs[32];
+  for (int j = 0; j < m; ++j) {
+    ptrs[j] = c->fcg + (size_t)j * n;            // P_j
+    ptrs[16 + j] = c->fcg + (size_t)(m + j) * n;  // AP_j
+  }
+  e = cudaMemcpy(c->fcg_ptrs, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "fcg pointers");
+  c->fcg_m = m;
   return TN_OK;
 }
 
@@ -252,6 +294,7 @@ void tn_destroy(tn_ctx *c) {
   free_ws(c);
   free_mesh(c);
   dfree(c->d_layer_c);
+  dfree(c->d_layer_c32);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->sstream) cudaStreamDestroy(c->sstream);
@@ -269,6 +312,7 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
   free_mesh(c);
   free_ws(c);
   dfree(c->d_layer_c);
+  dfree(c->d_layer_c32);
   c->have_mat = false;
   c->hm = hm;
   const int N2 = hm.N * hm.N;
@@ -282,6 +326,20 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
   up((void **)&c->d_colnb, hm.colnb, sizeof(int) * 4 * hm.ncol);
   up((void **)&c->d_colnbf, hm.colnbf, sizeof(int) * 4 * hm.ncol);
   up((void **)&c->d_slab_layer, hm.slab_layer, sizeof(int) * hm.nslab);
+  {
+    const size_t ncg = (size_t)hm.ncol * CG_NF * N2, nsg = (size_t)hm.nslab * SG_NF * hm.N;
+    float *f32 = (float *)std::malloc(sizeof(float) * (ncg > nsg ? ncg : nsg));
+    if (!f32) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+      for (size_t q = 0; q < ncg; ++q) f32[q] = (float)hm.colgeo[q];
+      up((void **)&c->d_colgeo32, f32, sizeof(float) * ncg);
+    }
+    if (e == cudaSuccess) {
+      for (size_t q = 0; q < nsg; ++q) f32[q] = (float)hm.slabgeo[q];
+      up((void **)&c->d_slabgeo32, f32, sizeof(float) * nsg);
+    }
+    std::free(f32);
+  }
   if (e != cudaSuccess) {
     free_mesh(c);
     return cuda_fail(e, "uploading the mesh");
@@ -299,6 +357,8 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
   m.bc_side = hm.bc_side; m.bc_bottom = hm.bc_bottom; m.penC = hm.penC;
   m.colgeo = c->d_colgeo; m.slabgeo = c->d_slabgeo; m.colnb = c->d_colnb; m.colnbf = c->d_colnbf;
   m.slab_layer = c->d_slab_layer; m.layer_c = nullptr;
+  m.colgeo32 = c->d_colgeo32; m.slabgeo32 = c->d_slabgeo32; m.layer_c32 = nullptr;
+  m.penC32 = (float)hm.penC;
   c->ndof = (size_t)3 * hm.N * hm.N * hm.N * hm.E;
   c->have_mesh = true;
   return TN_OK;
@@ -344,11 +404,18 @@ tn_status tn_set_materials(tn_ctx *c, int n, const tn_material *mats) {
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   CU_TRY(cudaStreamSynchronize(c->stream), "sync before replacing materials");
   dfree(c->d_layer_c);
+  dfree(c->d_layer_c32);
+  float h32[3 * 4096];
+  if (n > 4096) { std::free(h); return fail(TN_EINVAL, "at most 4096 layers"); }
+  for (int i = 0; i < 3 * n; ++i) h32[i] = (float)h[i];
   cudaError_t e = cudaMalloc((void **)&c->d_layer_c, sizeof(double) * 3 * n);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_layer_c, h, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_layer_c32, sizeof(float) * 3 * n);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_layer_c32, h32, sizeof(float) * 3 * n, cudaMemcpyHostToDevice);
   std::free(h);
   if (e != cudaSuccess) return cuda_fail(e, "uploading materials");
   c->dm.layer_c = c->d_layer_c;
+  c->dm.layer_c32 = c->d_layer_c32;
   c->have_mat = true;
   free_precond(c);
   return TN_OK;
@@ -480,44 +547,73 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
     r.status = energy_done ? 1 : 0;
   } else {
     CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
-    if (!o->use_x0) CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
+    const int m = o->fcg_window > 0 ? (o->fcg_window > 16 ? 16 : o->fcg_window) : 8;
+    const int kin = o->inner_max > 0 ? o->inner_max : 30;
+    if ((st = ensure_fcg(c, m))) return st;
+    double *P0 = c->fcg, *AP0 = c->fcg + (size_t)m * n;
+    // r = b - A x
+    if (!o->use_x0) {
+      CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
+      CU_TRY(cudaMemcpyAsync(c->r64, c->b64, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "r = b");
+    } else {
+      double rr0;
+      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr0, s), "residual");
+      r.applies_f64 += 1;
+    }
     int total_inner = 0;
     EnergyTrack et{c, u, s, o->energy_rtol};
-    double best = INFINITY;
+    double best = INFINITY, pAp[16];
     int stall = 0;
     bool energy_done = false;
-    for (int outer = 0; outer < o->max_outer; ++outer) {
+    for (int k = 0; k < o->max_outer; ++k) {
       double rr = 0.0;
-      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
-      r.applies_f64 += 1;
+      CU_TRY(tn::norm2_f64(n, c->r64, c->part_red, c->sum_dev, &rr, s), "norm r");
       r.rel_residual = std::sqrt(rr / bb);
       if (!std::isfinite(rr)) { result = fail(TN_EBREAKDOWN, "non-finite residual"); break; }
       if (r.rel_residual <= o->rtol) break;
-      if (o->energy_rtol > 0.0 && outer > 0) {
+      if (o->energy_rtol > 0.0 && k > 0) {
         energy_done = et.step();
         CU_TRY(et.err, "energy check");
         r.energy_change = et.change;
         if (energy_done) break;
       }
-      // stagnation: the FP64 residual has reached its rounding floor
       if (r.rel_residual < 0.5 * best) { best = r.rel_residual; stall = 0; }
-      else if (++stall >= 3) break;
+      else if (++stall >= 30) break;  // FP64 rounding floor reached
       if (total_inner >= o->max_iter) break;
+      // inner FP32 PCG on A d = r / |r|
       const double rn = std::sqrt(rr);
       CU_TRY(tn::cast_scaled(n, c->r64, 1.0 / rn, c->b32, c->d32, s), "cast");
       PcgVectors v{c->d32, c->r32, c->z32, c->p32, c->q32, c->b32, c->dinv32};
       if (zl) { v.zfac = c->zfac; v.part_rz = c->zpart; }
       int applies = 0;
-      CU_TRY(tn::pcg_f32(c->dm, n, v, true, o->inner_rtol, o->max_iter - total_inner, chunk, c->scal,
-                         c->scal_host, c->part_elem, c->part_red, s, &applies), "pcg f32");
+      CU_TRY(tn::pcg_f32(c->dm, n, v, true, o->inner_rtol, kin, kin, c->scal, c->scal_host, c->part_elem,
+                         c->part_red, s, &applies), "pcg f32");
       total_inner += c->scal_host->iters;
       r.applies_f32 += applies;
       r.outer_iters += 1;
-      if (c->scal_host->breakdown && c->scal_host->iters == 0) {
-        result = fail(TN_EBREAKDOWN, "inner CG breakdown");
-        break;
+      // z = |r| d (FP64), q = A z
+      CU_TRY(tn::upcast(n, c->d32, rn, c->z64, s), "upcast");
+      CU_TRY(tn_launch_apply(c->dm, TN_F64, c->z64, c->q64, nullptr, nullptr, s), "apply f64");
+      tn::g_launches += 1;
+      r.applies_f64 += 1;
+      // keep the new direction A-orthogonal to the last nb ones
+      const int nb = k < m ? k : m, slot = k % m;
+      double beta[16];
+      if (nb > 0) {
+        double zAp[16];
+        CU_TRY(tn::multidot(n, c->z64, c->fcg_ptrs + 16, nb, c->fcg_part, c->fcg_host, zAp, s), "dots");
+        for (int j = 0; j < nb; ++j) beta[j] = zAp[j] / pAp[j];
+        CU_TRY(cudaMemcpyAsync(c->fcg_beta, beta, sizeof(double) * nb, cudaMemcpyHostToDevice, s), "beta");
       }
-      CU_TRY(tn::refine_update(n, u, c->d32, rn, s), "refine");
+      CU_TRY(tn::fcg_orth(n, c->z64, c->q64, c->fcg_ptrs, c->fcg_ptrs + 16, c->fcg_beta, nb,
+                          P0 + (size_t)slot * n, AP0 + (size_t)slot * n, s), "orth");
+      const double *pair[2] = {c->r64, AP0 + (size_t)slot * n};
+      CU_TRY(cudaMemcpyAsync(c->fcg_ptrs + 32, pair, sizeof(pair), cudaMemcpyHostToDevice, s), "pair");
+      double d2[2];
+      CU_TRY(tn::multidot(n, P0 + (size_t)slot * n, c->fcg_ptrs + 32, 2, c->fcg_part, c->fcg_host, d2, s), "dots");
+      if (!(d2[1] > 0.0)) { result = fail(TN_EBREAKDOWN, "flexible CG breakdown (p.Ap = %g)", d2[1]); break; }
+      pAp[slot] = d2[1];
+      CU_TRY(tn::fcg_step(n, d2[0] / d2[1], P0 + (size_t)slot * n, AP0 + (size_t)slot * n, u, c->r64, s), "step");
     }
     r.inner_iters = total_inner;
     r.status = energy_done ? 1 : 0;

@@ -63,12 +63,33 @@ __device__ __forceinline__ T slab_dz(const DevMesh &m, int s, int k) {
   return (T)m.slabgeo[((size_t)s * SG_NF + SG_DZ) * m.N + k];
 }
 template <>
+__device__ __forceinline__ float slab_dz<float>(const DevMesh &m, int s, int k) {
+  return m.slabgeo32[((size_t)s * SG_NF + SG_DZ) * m.N + k];
+}
+template <>
 __device__ __forceinline__ Dual slab_dz<Dual>(const DevMesh &m, int s, int k) {
   return Dual(m.slabgeo[((size_t)s * SG_NF + SG_DZ) * m.N + k], m.d_slabdz ? m.d_slabdz[(size_t)s * m.N + k] : 0.0);
 }
 template <typename T>
 __device__ __forceinline__ T layer_coef(const DevMesh &m, int L, int q) {
   return (T)m.layer_c[3 * L + q];
+}
+template <>
+__device__ __forceinline__ float layer_coef<float>(const DevMesh &m, int L, int q) {
+  return m.layer_c32[3 * L + q];
+}
+// column geometry table in the kernel's precision
+template <typename T> struct ColGeo { using type = double; };
+template <> struct ColGeo<float> { using type = float; };
+template <typename T>
+__device__ __forceinline__ const typename ColGeo<T>::type *col_table(const DevMesh &m) {
+  if constexpr (std::is_same<T, float>::value) return m.colgeo32;
+  else return m.colgeo;
+}
+template <typename T>
+__device__ __forceinline__ T pen_const(const DevMesh &m) {
+  if constexpr (std::is_same<T, float>::value) return m.penC32;
+  else return T(m.penC);
 }
 template <>
 __device__ __forceinline__ Dual layer_coef<Dual>(const DevMesh &m, int L, int q) {
@@ -272,7 +293,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
     if (d2 == 2) {
       h2 = T(2) * slab_dz<T>(m, fi.nbslab[f], end);
     } else {
-      const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
+      const auto *g2 = col_table<T>(m) + (size_t)fi.nbcol[f] * CG_NF * N2;
       const int q2 = j2 * N + i2;
       const T rx = (T)g2[(d2 == 0 ? CG_IXX : CG_IEX) * N2 + q2];
       const T ry = (T)g2[(d2 == 0 ? CG_IXY : CG_IEY) * N2 + q2];
@@ -282,7 +303,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
   }
   __syncthreads();
 
-  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const auto *cg = col_table<T>(m) + (size_t)c * CG_NF * N2;
   const int Lown = m.slab_layer[s];
   const T c11 = layer_coef<T>(m, Lown, 0), c12 = layer_coef<T>(m, Lown, 1), c44 = layer_coef<T>(m, Lown, 2);
 
@@ -330,7 +351,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) { deta[cc] = dn[cc]; dxi[cc] = sg1 * dt1[cc]; dzeta[cc] = dt2[cc]; }
       }
-      const double *g2 = m.colgeo + (size_t)fi.nbcol[f] * CG_NF * N2;
+      const auto *g2 = col_table<T>(m) + (size_t)fi.nbcol[f] * CG_NF * N2;
       const int q2 = j2 * N + i2;
       jxx = (T)g2[CG_IXX * N2 + q2]; jxy = (T)g2[CG_IXY * N2 + q2];
       jex = (T)g2[CG_IEX * N2 + q2]; jey = (T)g2[CG_IEY * N2 + q2];
@@ -382,7 +403,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
     const bool onface = i == 0 || i == N - 1 || j == 0 || j == N - 1 || k == 0 || k == N - 1;
     if (onface) {
       const Sym<T> sig = stress(S, c11, c12, c44);
-      const T sp1 = T((m.p + 1) * (m.p + 1)) * (T)m.penC;
+      const T sp1 = T((float)((m.p + 1) * (m.p + 1))) * pen_const<T>(m);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int idx = d == 0 ? i : (d == 1 ? j : k);
@@ -441,6 +462,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
 
   // ---- weak divergence: y = sum_m D_m^T F^m
   double dot = 0.0;
+  T dott = T(0);
   if (active) {
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
@@ -456,10 +478,11 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
         dot += acc.d * lam[(size_t)e * 3 * n + cc * n + p];
       } else {
         y[(size_t)e * 3 * n + cc * n + p] = acc;
-        dot += (double)acc * (double)su[cc * n + p];
+        dott += acc * su[cc * n + p];
       }
     }
   }
+  if constexpr (!std::is_same<T, Dual>::value) dot = (double)dott;
   if (partial) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);

@@ -290,7 +290,7 @@ zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, const T *__restri
   const int line = blockIdx.x * 4 + warp;
   const int nlines = m.ncol * N2;
   const int S = m.nslab;
-  double rz = 0.0;
+  T rzt = T(0);
   if (line < nlines) {
     const int c = line / N2, q = line - c * N2, i = q % N, j = q / N;
     const int a = lane / N, k = lane - (lane / N) * N;
@@ -345,11 +345,12 @@ zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, const T *__restri
       }
       if (act) {
         z[idx] = x;
-        rz += (double)r[idx] * (double)x;
+        rzt += r[idx] * x;
       }
       xn = x;
     }
   }
+  double rz = (double)rzt;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
   if (lane == 0) red[warp] = rz;

@@ -73,13 +73,15 @@ __global__ void k_alpha(tn_pcg_scalars *s, const double *partial, int n) {
   }
 }
 
+// per-thread accumulation in the vector precision (GB300's FP64 pipe is too
+// narrow for per-element conversions), FP64 across threads in a fixed order
 template <typename T>
 __global__ void k_update(tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__restrict__ r,
                          T *__restrict__ z, const T *__restrict__ p, const T *__restrict__ q,
                          const T *__restrict__ dinv, double *part) {
   if (s->done) return;
   const T alpha = (T)s->alpha;
-  double rz = 0.0, rr = 0.0;
+  T rzt = T(0), rrt = T(0);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const T xv = x[t] + alpha * p[t];
     const T rv = r[t] - alpha * q[t];
@@ -87,9 +89,10 @@ __global__ void k_update(tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__re
     x[t] = xv;
     r[t] = rv;
     z[t] = zv;
-    rz += (double)rv * (double)zv;
-    rr += (double)rv * (double)rv;
+    rzt += rv * zv;
+    rrt += rv * rv;
   }
+  double rz = (double)rzt, rr = (double)rrt;
   block_sum2(rz, rr);
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = rz;
@@ -233,19 +236,74 @@ __global__ void k_fill(size_t n, T *__restrict__ v, T val) {
 }
 
 
+// ---- flexible CG (FP64 outer of the mixed-precision solve)
+// dots[j] partials: a . B_j for up to 16 vectors B_j, fixed partition
+__global__ void k_multidot(size_t n, const double *__restrict__ a, const double *const *__restrict__ B, int nb,
+                           double *part) {
+  __shared__ double red[16][8];
+  double acc[16];
+  for (int j = 0; j < nb; ++j) acc[j] = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double av = a[t];
+    for (int j = 0; j < nb; ++j) acc[j] += av * B[j][t];
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int j = 0; j < nb; ++j) {
+    double v = warp_sum(acc[j]);
+    if (l == 0) red[j][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    double v = 0.0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += red[threadIdx.x][ww];
+    part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// p = z - sum_j beta_j P_j,  Ap = q - sum_j beta_j AP_j
+__global__ void k_fcg_orth(size_t n, const double *__restrict__ z, const double *__restrict__ q,
+                           const double *const *__restrict__ P, const double *const *__restrict__ AP,
+                           const double *__restrict__ beta, int nb, double *__restrict__ p, double *__restrict__ Ap) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    double pv = z[t], av = q[t];
+    for (int j = 0; j < nb; ++j) {
+      pv -= beta[j] * P[j][t];
+      av -= beta[j] * AP[j][t];
+    }
+    p[t] = pv;
+    Ap[t] = av;
+  }
+}
+
+// x += alpha p, r -= alpha Ap
+__global__ void k_fcg_step(size_t n, double alpha, const double *__restrict__ p, const double *__restrict__ Ap,
+                           double *__restrict__ x, double *__restrict__ r) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    x[t] += alpha * p[t];
+    r[t] -= alpha * Ap[t];
+  }
+}
+
+// z64 = scale * d32
+__global__ void k_upcast(size_t n, const float *__restrict__ d, double scale, double *__restrict__ z) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    z[t] = scale * (double)d[t];
+}
+
 // ---- variants for a preconditioner applied by a separate kernel (z-line)
 template <typename T>
 __global__ void k_update_r(tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__restrict__ r,
                            const T *__restrict__ p, const T *__restrict__ q, double *part) {
   if (s->done) return;
   const T alpha = (T)s->alpha;
-  double rr = 0.0, dummy = 0.0;
+  T rrt = T(0);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     x[t] += alpha * p[t];
     const T rv = r[t] - alpha * q[t];
     r[t] = rv;
-    rr += (double)rv * (double)rv;
+    rrt += rv * rv;
   }
+  double rr = (double)rrt, dummy = 0.0;
   block_sum2(rr, dummy);
   if (threadIdx.x == 0) part[blockIdx.x] = rr;
 }
@@ -402,19 +460,47 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
   TN_CU(cudaStreamSynchronize(st));
   if (s_host->done) return cudaSuccess;
 
-  cudaGraph_t graph = nullptr;
+  // one graph of `chunk` iterations, cached while the run's buffers are unchanged
+  struct Key {
+    const void *x, *r, *z, *p, *q, *b, *dinv, *zfac;
+    const double *part_rz, *pe, *pr;
+    const void *s;
+    size_t n;
+    int chunk, prec, E;
+    const void *geo;
+    DevMesh dm;  // baked into the captured kernel parameters
+    bool operator==(const Key &o) const { return std::memcmp(this, &o, sizeof(Key)) == 0; }
+  };
+  Key key;
+  std::memset(&key, 0, sizeof(key));
+  key.x = v.x; key.r = v.r; key.z = v.z; key.p = v.p; key.q = v.q; key.b = v.b; key.dinv = v.dinv;
+  key.zfac = v.zfac; key.part_rz = v.part_rz; key.pe = part_elem; key.pr = part_red; key.s = s_dev;
+  key.n = n; key.chunk = chunk; key.prec = prec; key.E = m.E; key.geo = m.colgeo;
+  std::memcpy(&key.dm, &m, sizeof(DevMesh));
+  static thread_local Key cached_key[2];
+  static thread_local cudaGraphExec_t cached_exec[2] = {nullptr, nullptr};
+  const int slot = prec == TN_F64 ? 0 : 1;
   cudaGraphExec_t exec = nullptr;
-  TN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t cap = cudaSuccess;
-  for (int it = 0; it < chunk && cap == cudaSuccess; ++it)
-    cap = zl ? pcg_iteration_zline<T>(m, prec, n, v, s_dev, part_elem, part_red, st)
-             : pcg_iteration<T>(m, prec, n, v, s_dev, part_elem, part_red, st);
-  cudaError_t endc = cudaStreamEndCapture(st, &graph);
-  if (cap != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cap; }
-  TN_CU(endc);
-  cudaError_t err = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  TN_CU(err);
+  cudaError_t err = cudaSuccess;
+  if (cached_exec[slot] && cached_key[slot] == key) {
+    exec = cached_exec[slot];
+  } else {
+    if (cached_exec[slot]) { cudaGraphExecDestroy(cached_exec[slot]); cached_exec[slot] = nullptr; }
+    cudaGraph_t graph = nullptr;
+    TN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t cap = cudaSuccess;
+    for (int it = 0; it < chunk && cap == cudaSuccess; ++it)
+      cap = zl ? pcg_iteration_zline<T>(m, prec, n, v, s_dev, part_elem, part_red, st)
+               : pcg_iteration<T>(m, prec, n, v, s_dev, part_elem, part_red, st);
+    cudaError_t endc = cudaStreamEndCapture(st, &graph);
+    if (cap != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cap; }
+    TN_CU(endc);
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TN_CU(err);
+    cached_exec[slot] = exec;
+    cached_key[slot] = key;
+  }
   double best = INFINITY;
   int stall = 0;
   for (;;) {
@@ -431,7 +517,6 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     if (s_host->rr < 0.5 * best) { best = s_host->rr; stall = 0; }
     else if (++stall >= 40) break;
   }
-  cudaGraphExecDestroy(exec);
   *applies += s_host->iters;
   return err;
 }
@@ -499,6 +584,42 @@ cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st) {
 }
 
 int reduction_blocks() { return kRedBlocks; }
+
+// dots a . B_j (j < nb <= 16) summed in a fixed order on the host
+cudaError_t multidot(size_t n, const double *a, const double *const *B_dev, int nb, double *part, double *host_tmp,
+                     double *out, cudaStream_t st) {
+  g_launches += 1;
+  k_multidot<<<kRedBlocks, kRedThreads, 0, st>>>(n, a, B_dev, nb, part);
+  TN_CU(cudaGetLastError());
+  TN_CU(cudaMemcpyAsync(host_tmp, part, sizeof(double) * nb * kRedBlocks, cudaMemcpyDeviceToHost, st));
+  TN_CU(cudaStreamSynchronize(st));
+  for (int j = 0; j < nb; ++j) {
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += host_tmp[(size_t)j * kRedBlocks + b];
+    out[j] = s;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t fcg_orth(size_t n, const double *z, const double *q, const double *const *P, const double *const *AP,
+                     const double *beta, int nb, double *p, double *Ap, cudaStream_t st) {
+  g_launches += 1;
+  k_fcg_orth<<<kRedBlocks, kRedThreads, 0, st>>>(n, z, q, P, AP, beta, nb, p, Ap);
+  return cudaGetLastError();
+}
+
+cudaError_t fcg_step(size_t n, double alpha, const double *p, const double *Ap, double *x, double *r,
+                     cudaStream_t st) {
+  g_launches += 1;
+  k_fcg_step<<<kRedBlocks, kRedThreads, 0, st>>>(n, alpha, p, Ap, x, r);
+  return cudaGetLastError();
+}
+
+cudaError_t upcast(size_t n, const float *d, double scale, double *z, cudaStream_t st) {
+  g_launches += 1;
+  k_upcast<<<kRedBlocks, kRedThreads, 0, st>>>(n, d, scale, z);
+  return cudaGetLastError();
+}
 
 }  // namespace tn
 

@@ -45,6 +45,12 @@ struct DevMesh {
   const int *colnbf;      // [ncol][4]: neighbour face (0..3) | (flip << 2)
   const int *slab_layer;  // [nslab]
   const double *layer_c;  // [n_layers][3]: c11, c12, c44 (isotropic: lambda+2mu, lambda, mu)
+  // FP32 copies of the tables for the FP32 kernels (GB300's FP64 pipe is
+  // too narrow for per-node double -> float conversions)
+  const float *colgeo32 = nullptr;
+  const float *slabgeo32 = nullptr;
+  const float *layer_c32 = nullptr;
+  float penC32 = 0.0f;
   // forward-mode seeds for derivative kernels (nullptr: no dependence)
   const double *d_slabdz = nullptr;  // [nslab][N]: d(dz/dzeta)/dtheta at each node
   const double *d_layer_c = nullptr;  // [n_layers][3]: d(c11, c12, c44)/dtheta

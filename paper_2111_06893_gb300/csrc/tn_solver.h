@@ -47,4 +47,11 @@ cudaError_t cast_scaled(size_t n, const double *r64, double scale, float *r32, f
 cudaError_t refine_update(size_t n, double *x, const float *d, double scale, cudaStream_t st);
 cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st);
 int reduction_blocks();
+cudaError_t multidot(size_t n, const double *a, const double *const *B_dev, int nb, double *part, double *host_tmp,
+                     double *out, cudaStream_t st);
+cudaError_t fcg_orth(size_t n, const double *z, const double *q, const double *const *P, const double *const *AP,
+                     const double *beta, int nb, double *p, double *Ap, cudaStream_t st);
+cudaError_t fcg_step(size_t n, double alpha, const double *p, const double *Ap, double *x, double *r,
+                     cudaStream_t st);
+cudaError_t upcast(size_t n, const float *d, double scale, double *z, cudaStream_t st);
 }  // namespace tn

@@ -49,7 +49,8 @@ class Material(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
-                ("use_x0", C.c_int), ("check_every", C.c_int), ("energy_rtol", C.c_double)]
+                ("use_x0", C.c_int), ("check_every", C.c_int), ("inner_max", C.c_int),
+                ("fcg_window", C.c_int), ("energy_rtol", C.c_double)]
 
 
 class SolveReport(C.Structure):
@@ -278,15 +279,16 @@ class Context:
             _check(st)
         return {"slab_z": gz, "r0": float(gr[0]), "moduli": gm.reshape(nl, 3), "report": rep.as_dict()}
 
-    def solve(self, mode="f64", rtol=1e-12, inner_rtol=0.05, max_iter=200000, max_outer=60,
+    def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",
-              energy_rtol=0.0):
+              energy_rtol=0.0, inner_max=30, fcg_window=8):
         o = SolveOpts()
         o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
         o.precond = PRECONDS[precond]
         o.rtol, o.inner_rtol = rtol, inner_rtol
         o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
         o.energy_rtol = energy_rtol
+        o.inner_max, o.fcg_window = inner_max, fcg_window
         u = out if out is not None else self._vec(self._torch.float64)
         o.use_x0 = 0
         if x0 is not None:
