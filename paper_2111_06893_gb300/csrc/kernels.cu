@@ -96,6 +96,16 @@ __device__ __forceinline__ Dual layer_coef<Dual>(const DevMesh &m, int L, int q)
   return Dual(m.layer_c[3 * L + q], m.d_layer_c ? m.d_layer_c[3 * L + q] : 0.0);
 }
 
+// min(h, h_ext) of Eq. (penalty).  At an exact tie the dual number takes the
+// smaller derivative: the one-sided derivative for an increasing parameter,
+// the same on both sides of the face (so dA/dtheta stays symmetric)
+template <typename T>
+__device__ __forceinline__ T hmin(T a, T b) { return a < b ? a : b; }
+template <>
+__device__ __forceinline__ Dual hmin<Dual>(Dual a, Dual b) {
+  return (a.v < b.v || (a.v == b.v && a.d <= b.d)) ? a : b;
+}
+
 // symmetric tensors as (xx, yy, zz, xy, xz, yz)
 template <typename T> struct Sym { T xx, yy, zz, xy, xz, yz; };
 
@@ -434,7 +444,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
           for (int cc = 0; cc < 3; ++cc) { jump[cc] = uo[cc] + uo[cc]; tr2[cc] = tr[cc]; }
           h2 = h; y11 = c11; y12 = c12; y44 = c44;
         }
-        const T sigma = sp1 / (h < h2 ? h : h2);
+        const T sigma = sp1 / hmin<T>(h, h2);
         const Sym<T> Ej = sym_outer(nrm, jump);
         const Sym<T> Sj = stress(Ej, y11, y12, y44);
         T pen[3];
@@ -496,6 +506,367 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Second form of the operator kernel for T = float / double.  Same arithmetic
+// as apply_kernel, reorganised so that every sum-factorised contraction is a
+// "line task": one thread owns a whole line of N nodes along one logical
+// direction, keeps it in registers and produces all N outputs with the
+// derivative matrix as compile-time (warp-uniform) constant operands.  This
+// removes the per-thread-indexed constant loads and cuts shared-memory traffic
+// about threefold.  Phases (one CTA per element, one thread per node):
+//   1  gather neighbour face values / normal derivatives  +  gradient lines
+//   2  neighbour tangential derivative lines on the face planes
+//   3  neighbour traction at the face nodes
+//   4  per node: strain, stress, face terms, lifted strain, fluxes
+//   5  weak-divergence lines (one partial sum per direction)
+//   6  per node: sum the three directions and the face terms, store y
+template <int N, typename T>
+constexpr size_t apply2_smem() {
+  return sizeof(T) * (3 * N * N * N + 9 * N * N * N + 9 * N * N * N + 18 * N * N * 4 + 6 * N * N);
+}
+
+// out[a'] = sum_a D[a'][a] v[a]   (derivative along the line)
+template <int N, typename T>
+__device__ __forceinline__ void line_diff(const T v[N], T out[N]) {
+#pragma unroll
+  for (int a2 = 0; a2 < N; ++a2) {
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc += Tab<T>::D(N, a2, a) * v[a];
+    out[a2] = acc;
+  }
+}
+// out[a'] = sum_a D[a][a'] v[a]   (transposed: weak divergence along the line)
+template <int N, typename T>
+__device__ __forceinline__ void line_difft(const T v[N], T out[N]) {
+#pragma unroll
+  for (int a2 = 0; a2 < N; ++a2) {
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc += Tab<T>::D(N, a, a2) * v[a];
+    out[a2] = acc;
+  }
+}
+
+// node index of position a on line l of direction d (l enumerates the N^2 lines)
+template <int N>
+__device__ __forceinline__ int line_node(int d, int l, int a) {
+  const int hi = l / N, lo = l - hi * N;
+  if (d == 0) return (hi * N + lo) * N + a;   // (k, j) fixed, i = a
+  if (d == 1) return (hi * N + a) * N + lo;   // (k, i) fixed, j = a
+  return (a * N + hi) * N + lo;               // (j, i) fixed, k = a
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(nthreads<N>())
+apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *su = reinterpret_cast<T *>(smem_raw);  // [3][n]
+  T *sG = su + 3 * n;                        // [3 dir][3 comp][n] logical gradient, then fluxes F^m_j
+  T *sY = sG + 9 * n;                        // [3 dir][3 comp][n] divergence partial sums
+  T *nbv = sY + 9 * n;                       // [6][3][N2] neighbour face values
+  T *nbt = nbv + 18 * N2;                    // [6][3][N2] normal derivative, then traction
+  T *nbd = nbt + 18 * N2;                    // [2][6][3][N2] tangential derivatives
+  T *nbh = nbd + 36 * N2;                    // [6][N2]
+  __shared__ FaceInfo fi;
+  __shared__ T nbc[6][3];
+  __shared__ double red[NT / 32];
+
+  const int e = e0 + blockIdx.x, tid = threadIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  const T *ue = u + (size_t)e * 3 * n;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = ue[t];
+  if (tid < 6) {
+    face_info(m, s, c, fi, tid);
+    const int L = m.slab_layer[fi.nbslab[tid]];
+    nbc[tid][0] = layer_coef<T>(m, L, 0);
+    nbc[tid][1] = layer_coef<T>(m, L, 1);
+    nbc[tid][2] = layer_coef<T>(m, L, 2);
+  }
+  __syncthreads();
+
+  // ---- phase 1: neighbour gather tasks [0, 6 N2) and gradient line tasks [6 N2, 6 N2 + 9 N2)
+  for (int t = tid; t < 15 * N2; t += NT) {
+    if (t < 6 * N2) {
+      const int f = t / N2, q = t - f * N2;
+      if (fi.kind[f] != FK_INTERIOR) continue;
+      const int t1 = q % N, t2 = q / N;
+      const int f2 = fi.nbface[f], d2 = f2 >> 1, end = (f2 & 1) ? N - 1 : 0;
+      int i2, j2, k2;
+      if ((f >> 1) == 2) { i2 = t1; j2 = t2; k2 = end; }
+      else {
+        const int a = fi.flip[f] ? N - 1 - t1 : t1;
+        k2 = t2;
+        if (d2 == 0) { i2 = end; j2 = a; } else { i2 = a; j2 = end; }
+      }
+      const T *u2 = u + (size_t)fi.nb[f] * 3 * n;
+      const int stride = d2 == 0 ? 1 : (d2 == 1 ? N : N2);
+      const int base = (k2 * N + j2) * N + i2 - end * stride;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        T line[N];
+#pragma unroll
+        for (int mm = 0; mm < N; ++mm) line[mm] = u2[cc * n + base + mm * stride];
+        T dn = T(0);
+        if (end == 0) {
+#pragma unroll
+          for (int mm = 0; mm < N; ++mm) dn += Tab<T>::D(N, 0, mm) * line[mm];
+          nbv[(f * 3 + cc) * N2 + q] = line[0];
+        } else {
+#pragma unroll
+          for (int mm = 0; mm < N; ++mm) dn += Tab<T>::D(N, N - 1, mm) * line[mm];
+          nbv[(f * 3 + cc) * N2 + q] = line[N - 1];
+        }
+        nbt[(f * 3 + cc) * N2 + q] = dn;
+      }
+      T h2;
+      if (d2 == 2) {
+        h2 = T(2) * slab_dz<T>(m, fi.nbslab[f], end);
+      } else {
+        const auto *g2 = col_table<T>(m) + (size_t)fi.nbcol[f] * CG_NF * N2;
+        const int q2 = j2 * N + i2;
+        const T rx = (T)g2[(d2 == 0 ? CG_IXX : CG_IEX) * N2 + q2];
+        const T ry = (T)g2[(d2 == 0 ? CG_IXY : CG_IEY) * N2 + q2];
+        h2 = T(2) / sqrt(rx * rx + ry * ry);
+      }
+      nbh[f * N2 + q] = h2;
+    } else {
+      const int tt = t - 6 * N2, d = tt / (3 * N2), rem = tt - d * 3 * N2, cc = rem / N2, l = rem - cc * N2;
+      const T *v = su + cc * n;
+      T in[N], out[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) in[a] = v[line_node<N>(d, l, a)];
+      line_diff<N, T>(in, out);
+      T *g = sG + (d * 3 + cc) * n;
+#pragma unroll
+      for (int a = 0; a < N; ++a) g[line_node<N>(d, l, a)] = out[a];
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: tangential derivatives of the neighbour face values
+  for (int t = tid; t < 36 * N; t += NT) {
+    const int f = t / (6 * N), rem = t - f * 6 * N, cc = rem / (2 * N), r2 = rem - cc * 2 * N;
+    const int dir = r2 / N, l = r2 - dir * N;
+    if (fi.kind[f] != FK_INTERIOR) continue;
+    const T *v = nbv + (f * 3 + cc) * N2;
+    T in[N], out[N];
+    if (dir == 0) {  // along t1, fixed t2 = l
+#pragma unroll
+      for (int a = 0; a < N; ++a) in[a] = v[l * N + a];
+    } else {         // along t2, fixed t1 = l
+#pragma unroll
+      for (int a = 0; a < N; ++a) in[a] = v[a * N + l];
+    }
+    line_diff<N, T>(in, out);
+    T *o = nbd + ((dir * 6 + f) * 3 + cc) * N2;
+    if (dir == 0) {
+#pragma unroll
+      for (int a = 0; a < N; ++a) o[l * N + a] = out[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < N; ++a) o[a * N + l] = out[a];
+    }
+  }
+  __syncthreads();
+
+  const auto *cg = col_table<T>(m) + (size_t)c * CG_NF * N2;
+  const int Lown = m.slab_layer[s];
+  const T c11 = layer_coef<T>(m, Lown, 0), c12 = layer_coef<T>(m, Lown, 1), c44 = layer_coef<T>(m, Lown, 2);
+
+  // ---- phase 3: neighbour traction n . Y_ext grad u_ext at the face nodes
+  for (int t = tid; t < 6 * N2; t += NT) {
+    const int f = t / N2, q = t - f * N2;
+    if (fi.kind[f] != FK_INTERIOR) continue;
+    const int t1 = q % N, t2 = q / N, d = f >> 1;
+    const int f2 = fi.nbface[f], d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+    T dt1[3], dt2[3], dn[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      dt1[cc] = nbd[((0 * 6 + f) * 3 + cc) * N2 + q];
+      dt2[cc] = nbd[((1 * 6 + f) * 3 + cc) * N2 + q];
+      dn[cc] = nbt[(f * 3 + cc) * N2 + q];
+    }
+    T dxi[3], deta[3], dzeta[3];
+    T jxx, jxy, jex, jey, jdz;
+    int i, j, k;
+    face_node<N>(f, t1, t2, i, j, k);
+    if (d == 2) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) { dxi[cc] = dt1[cc]; deta[cc] = dt2[cc]; dzeta[cc] = dn[cc]; }
+      const int qq = j * N + i;
+      jxx = (T)cg[CG_IXX * N2 + qq]; jxy = (T)cg[CG_IXY * N2 + qq];
+      jex = (T)cg[CG_IEX * N2 + qq]; jey = (T)cg[CG_IEY * N2 + qq];
+      jdz = T(1) / slab_dz<T>(m, fi.nbslab[f], end2);
+    } else {
+      const T sg1 = fi.flip[f] ? T(-1) : T(1);
+      const int a = fi.flip[f] ? N - 1 - t1 : t1;
+      int i2, j2;
+      if (d2 == 0) {
+        i2 = end2; j2 = a;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) { dxi[cc] = dn[cc]; deta[cc] = sg1 * dt1[cc]; dzeta[cc] = dt2[cc]; }
+      } else {
+        i2 = a; j2 = end2;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) { deta[cc] = dn[cc]; dxi[cc] = sg1 * dt1[cc]; dzeta[cc] = dt2[cc]; }
+      }
+      const auto *g2 = col_table<T>(m) + (size_t)fi.nbcol[f] * CG_NF * N2;
+      const int q2 = j2 * N + i2;
+      jxx = (T)g2[CG_IXX * N2 + q2]; jxy = (T)g2[CG_IXY * N2 + q2];
+      jex = (T)g2[CG_IEX * N2 + q2]; jey = (T)g2[CG_IEY * N2 + q2];
+      jdz = T(1) / slab_dz<T>(m, s, t2);
+    }
+    const Sym<T> S2 = strain(dxi, deta, dzeta, jxx, jxy, jex, jey, jdz);
+    const Sym<T> s2 = stress(S2, nbc[f][0], nbc[f][1], nbc[f][2]);
+    const int qq = j * N + i;
+    T nrm[3], W, h;
+    face_geom<T, N>(f, i, j, k, (T)cg[CG_IXX * N2 + qq], (T)cg[CG_IXY * N2 + qq],
+                    (T)cg[CG_IEX * N2 + qq], (T)cg[CG_IEY * N2 + qq], (T)cg[CG_DET * N2 + qq],
+                    slab_dz<T>(m, s, k), nrm, W, h);
+    T tr[3];
+    contract_n(s2, nrm, tr);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) nbt[(f * 3 + cc) * N2 + q] = tr[cc];
+  }
+  __syncthreads();
+
+  // ---- phase 4: per node
+  T ysurf[3] = {T(0), T(0), T(0)};
+  T uown[3] = {T(0), T(0), T(0)};
+  const int p = tid;
+  const bool active = p < n;
+  const int i = p % N, j = (p / N) % N, k = p / N2;
+  if (active) {
+    T dxi[3], deta[3], dzeta[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      dxi[cc] = sG[(0 * 3 + cc) * n + p];
+      deta[cc] = sG[(1 * 3 + cc) * n + p];
+      dzeta[cc] = sG[(2 * 3 + cc) * n + p];
+      uown[cc] = su[cc * n + p];
+    }
+    const int qq = j * N + i;
+    const T ixx = (T)cg[CG_IXX * N2 + qq], ixy = (T)cg[CG_IXY * N2 + qq];
+    const T iex = (T)cg[CG_IEX * N2 + qq], iey = (T)cg[CG_IEY * N2 + qq];
+    const T det2 = (T)cg[CG_DET * N2 + qq], dz = slab_dz<T>(m, s, k);
+    const T idz = T(1) / dz;
+    const Sym<T> S = strain(dxi, deta, dzeta, ixx, ixy, iex, iey, idz);
+    const T wJ = Tab<T>::w(N, i) * Tab<T>::w(N, j) * Tab<T>::w(N, k) * det2 * dz;
+    Sym<T> Se = {wJ * S.xx, wJ * S.yy, wJ * S.zz, wJ * S.xy, wJ * S.xz, wJ * S.yz};
+    const bool onface = i == 0 || i == N - 1 || j == 0 || j == N - 1 || k == 0 || k == N - 1;
+    if (onface) {
+      const Sym<T> sig = stress(S, c11, c12, c44);
+      const T sp1 = T((float)((m.p + 1) * (m.p + 1))) * pen_const<T>(m);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int idx = d == 0 ? i : (d == 1 ? j : k);
+        if (idx != 0 && idx != N - 1) continue;
+        const int f = 2 * d + (idx == N - 1 ? 1 : 0);
+        const int kind = fi.kind[f];
+        if (kind == FK_NEUMANN) continue;
+        T nrm[3], W, h;
+        face_geom<T, N>(f, i, j, k, ixx, ixy, iex, iey, det2, dz, nrm, W, h);
+        T tr[3];
+        contract_n(sig, nrm, tr);
+        const int t1 = d == 0 ? j : i, t2 = d == 2 ? j : k;
+        const int q = t2 * N + t1;
+        T jump[3], tr2[3], h2, y11, y12, y44;
+        if (kind == FK_INTERIOR) {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            jump[cc] = uown[cc] - nbv[(f * 3 + cc) * N2 + q];
+            tr2[cc] = nbt[(f * 3 + cc) * N2 + q];
+          }
+          h2 = nbh[f * N2 + q];
+          y11 = T(0.5) * (c11 + nbc[f][0]);
+          y12 = T(0.5) * (c12 + nbc[f][1]);
+          y44 = T(0.5) * (c44 + nbc[f][2]);
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) { jump[cc] = uown[cc] + uown[cc]; tr2[cc] = tr[cc]; }
+          h2 = h; y11 = c11; y12 = c12; y44 = c44;
+        }
+        const T sigma = sp1 / hmin<T>(h, h2);
+        const Sym<T> Ej = sym_outer(nrm, jump);
+        const Sym<T> Sj = stress(Ej, y11, y12, y44);
+        T pen[3];
+        contract_n(Sj, nrm, pen);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) ysurf[cc] -= W * (T(0.5) * (tr[cc] + tr2[cc]) - sigma * pen[cc]);
+        const T hw = T(-0.5) * W;
+        Se.xx += hw * Ej.xx; Se.yy += hw * Ej.yy; Se.zz += hw * Ej.zz;
+        Se.xy += hw * Ej.xy; Se.xz += hw * Ej.xz; Se.yz += hw * Ej.yz;
+      }
+    }
+    const Sym<T> se = stress(Se, c11, c12, c44);
+    // fluxes F^m_j overwrite the gradient at this node (read above by this thread only)
+    sG[(0 * 3 + 0) * n + p] = ixx * se.xx + ixy * se.xy;
+    sG[(0 * 3 + 1) * n + p] = ixx * se.xy + ixy * se.yy;
+    sG[(0 * 3 + 2) * n + p] = ixx * se.xz + ixy * se.yz;
+    sG[(1 * 3 + 0) * n + p] = iex * se.xx + iey * se.xy;
+    sG[(1 * 3 + 1) * n + p] = iex * se.xy + iey * se.yy;
+    sG[(1 * 3 + 2) * n + p] = iex * se.xz + iey * se.yz;
+    sG[(2 * 3 + 0) * n + p] = idz * se.xz;
+    sG[(2 * 3 + 1) * n + p] = idz * se.yz;
+    sG[(2 * 3 + 2) * n + p] = idz * se.zz;
+  }
+  __syncthreads();
+
+  // ---- phase 5: weak-divergence lines
+  for (int t = tid; t < 9 * N2; t += NT) {
+    const int d = t / (3 * N2), rem = t - d * 3 * N2, cc = rem / N2, l = rem - cc * N2;
+    const T *F = sG + (d * 3 + cc) * n;
+    T in[N], out[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) in[a] = F[line_node<N>(d, l, a)];
+    line_difft<N, T>(in, out);
+    T *o = sY + (d * 3 + cc) * n;
+#pragma unroll
+    for (int a = 0; a < N; ++a) o[line_node<N>(d, l, a)] = out[a];
+  }
+  __syncthreads();
+
+  // ---- phase 6: y = sum of the three directions + face terms
+  T dott = T(0);
+  if (active) {
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const T acc = ysurf[cc] + sY[(0 * 3 + cc) * n + p] + sY[(1 * 3 + cc) * n + p] + sY[(2 * 3 + cc) * n + p];
+      y[(size_t)e * 3 * n + cc * n + p] = acc;
+      dott += acc * uown[cc];
+    }
+  }
+  if (partial) {
+    double dot = (double)dott;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if ((tid & 31) == 0) red[tid >> 5] = dot;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < NT / 32; ++w) sum += red[w];
+      partial[blockIdx.x] = sum;
+    }
+  }
+}
+
+template <int N, typename T>
+cudaError_t launch_apply2(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+  constexpr size_t sm = apply2_smem<N, T>();
+  static int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t err = cudaFuncSetAttribute(apply2_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    configured_device = dev;
+  }
+  apply2_kernel<N, T><<<m.E, nthreads<N>(), sm, st>>>(m, 0, u, y, partial);
+  return cudaGetLastError();
+}
+
 template <int N, typename T, typename TIO>
 cudaError_t launch_apply_range(const DevMesh &m, int s0, int s1, const TIO *u, TIO *y, double *partial,
                                const double *lam, cudaStream_t st) {
@@ -517,7 +888,7 @@ cudaError_t launch_apply_range(const DevMesh &m, int s0, int s1, const TIO *u, T
 
 template <int N, typename T>
 cudaError_t launch_apply_n(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
-  return launch_apply_range<N, T, T>(m, 0, m.nslab, u, y, partial, nullptr, st);
+  return launch_apply2<N, T>(m, u, y, partial, st);
 }
 
 template <typename T>
@@ -648,7 +1019,7 @@ __global__ void diag_kernel(const DevMesh m, double *__restrict__ dg) {
       } else {
         h2 = h; y11 = c11; y44 = c44; fac = 1.0;
       }
-      const double sigma = sp1 / (h < h2 ? h : h2);
+      const double sigma = sp1 / hmin<double>(h, h2);
       for (int cc = 0; cc < 3; ++cc) {
         double Qc = 0.0;
         for (int a = 0; a < 3; ++a) Qc += (a == cc ? c11 : c44) * nrm[a] * g[a];

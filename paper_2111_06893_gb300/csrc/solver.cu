@@ -472,7 +472,7 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     bool operator==(const Key &o) const { return std::memcmp(this, &o, sizeof(Key)) == 0; }
   };
   Key key;
-  std::memset(&key, 0, sizeof(key));
+  std::memset(static_cast<void *>(&key), 0, sizeof(key));
   key.x = v.x; key.r = v.r; key.z = v.z; key.p = v.p; key.q = v.q; key.b = v.b; key.dinv = v.dinv;
   key.zfac = v.zfac; key.part_rz = v.part_rz; key.pe = part_elem; key.pr = part_red; key.s = s_dev;
   key.n = n; key.chunk = chunk; key.prec = prec; key.E = m.E; key.geo = m.colgeo;

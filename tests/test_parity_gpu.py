@@ -137,8 +137,8 @@ def test_solve_plain_box_energies_match_oracle_direct_solve(mode, precond):
     uo = ob.solve_dense(A, op.rhs())
     Uo = ob.layer_energies(op, uo)
     ctx = gpu_ctx(desc)
-    u, rep = ctx.solve(mode=mode, rtol=1e-13, precond=precond)
-    assert rep["rel_residual"] <= 1e-13
+    u, rep = ctx.solve(mode=mode, rtol=1e-12, energy_rtol=1e-12, precond=precond)
+    assert rep["rel_residual"] <= 1e-12 or rep["energy_change"] <= 1e-12
     U = ctx.layer_energies(u)
     assert np.max(np.abs(U - Uo) / Uo) < 1e-9, (U, Uo)
     un = u.cpu().numpy()
