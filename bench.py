@@ -37,6 +37,7 @@ WORKLOADS = {
     "plain_box": W.plain_box,
     "crystalline_multilayer": W.crystalline_multilayer,
     "large_mirror": W.large_mirror,
+    "design_sweep": lambda: W.design_sweep(256),
 }
 KB_T = 1.380649e-23 * 300.0
 FREQ = 100.0
@@ -203,6 +204,10 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup()
     desc = WORKLOADS[args.workload]()
+    descs = desc if isinstance(desc, list) else [desc]
+    batched = isinstance(desc, list)
+    if batched:
+        desc = descs[0]  # the CPU oracle samples the first mirror of a batch
     if args.impl == "reference":
         run_reference(args, desc, world, rank)
         return
@@ -221,9 +226,14 @@ def main():
         torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = thermonoise.setup(desc, device=local, stream=stream)
+    if batched:
+        ctx = thermonoise.Context(local, stream).build_batch(descs)
+    else:
+        ctx = thermonoise.setup(desc, device=local, stream=stream)
     ndof = ctx.ndof
     N = desc["degree"] + 1
+    dof_w = [W.n_dof(d) for d in descs]
+    flops_dof = sum(fp32_apply_flops_per_dof(d["degree"] + 1) * w for d, w in zip(descs, dof_w)) / sum(dof_w)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     if args.mode == "apply":
@@ -269,14 +279,16 @@ def main():
         err64 = float(np.max(np.abs(U64 - U_ref) / U_ref)) if U_ref is not None else None
         del u64
 
-    phi = np.array([4e-4] * (len(desc["materials"]) - 1) + [1e-6])
+    phis = [np.array([4e-4] * (len(d["materials"]) - 1) + [1e-6]) for d in descs]
+    lofs = np.cumsum([0] + [len(d["materials"]) for d in descs])
     u = torch.empty(ndof, dtype=torch.float64, device=dev)
 
     def step():
         _, rep = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u,
                            energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False)
         U = ctx.layer_energies(u)
-        S = thermonoise.noise_psd(U, phi, KB_T, FREQ, desc["beam"]["F0"])
+        S = [thermonoise.noise_psd(U[lofs[i]:lofs[i + 1]], phis[i], KB_T, FREQ, d["beam"]["F0"])
+             for i, d in enumerate(descs)]
         return rep, U, S
 
     for _ in range(args.warmup):
@@ -336,7 +348,7 @@ def main():
 
     t32 = time_apply(x32, y32, 200)
     t64 = time_apply(x64, y64, 20)
-    flops = fp32_apply_flops_per_dof(N) * ndof
+    flops = flops_dof * ndof
     sm_max = 2070.0
     peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
     achieved = flops / t32 / 1e12
@@ -344,22 +356,28 @@ def main():
 
     # ---- end to end through the C ABI with host buffers
     u_host = torch.empty(ndof, dtype=torch.float64, pin_memory=True)
-    ncol = W.n_columns(desc)
-    nslab = len(desc["slab_z"]) - 1
-    h2d = ncol * (7 * N * N * 8 + 8 * 4) + nslab * (2 * N * 8 + 4) + len(desc["materials"]) * 24
-    d2h = ndof * 8 + len(desc["materials"]) * 8
+    h2d = 0
+    for d in descs:
+        Nd = d["degree"] + 1
+        h2d += (W.n_columns(d) * (7 * Nd * Nd * 8 + 8 * 4) + (len(d["slab_z"]) - 1) * (2 * Nd * 8 + 4)
+                + len(d["materials"]) * 24)
+    d2h = ndof * 8 + int(lofs[-1]) * 8
     e2e_times = [(float("nan"), 0)]
     for it in range(0 if args.no_e2e else 2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.build_mesh(desc)
-        ctx.set_materials(desc["materials"])
-        ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
+        if batched:
+            ctx.build_batch(descs)
+        else:
+            ctx.build_mesh(desc)
+            ctx.set_materials(desc["materials"])
+            ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
         _, rep_e = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u,
                              energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False)
         u_host.copy_(u, non_blocking=True)
         U_e = ctx.layer_energies(u)
-        thermonoise.noise_psd(U_e, phi, KB_T, FREQ, desc["beam"]["F0"])
+        for i, d in enumerate(descs):
+            thermonoise.noise_psd(U_e[lofs[i]:lofs[i + 1]], phis[i], KB_T, FREQ, d["beam"]["F0"])
         torch.cuda.synchronize()
         e2e_times.append((time.perf_counter() - t0, rep_e["applies_f32"] + rep_e["applies_f64"]))
     e2e_value = e2e_times[-1][1] * ndof / e2e_times[-1][0] / 1e9 if not args.no_e2e else None
@@ -378,8 +396,10 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "ndof": ndof, "degree": desc["degree"],
-                   "elements": W.n_elements(desc), "step": "rhs+diag+mixed solve+energies+psd",
+        "config": {"workload": args.workload, "ndof": ndof,
+                   "degree": sorted({d["degree"] for d in descs}) if batched else desc["degree"],
+                   "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
+                   "step": "rhs+mixed solve+energies+psd",
                    "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
                    "precond": args.precond, "l2": "flushed between steps (256 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -397,8 +417,8 @@ def main():
                          "f32_gdofs": ndof / t32 / 1e9, "f64_gdofs": ndof / t64 / 1e9},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                      "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": f"apply_kernel<{N},float>",
-                     "flops_per_dof": fp32_apply_flops_per_dof(N),
+                     "kernel": "apply2_batch_kernel<N,float>" if batched else f"apply2_kernel<{N},float>",
+                     "flops_per_dof": flops_dof,
                      "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
                      "hbm_peak_GBps": peaks.get("hbm_gbs"),
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},

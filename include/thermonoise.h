@@ -223,6 +223,27 @@ tn_status tn_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const double *u
                          double *lambda_dev, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
                          tn_solve_report *rep);
 
+/* Batches (a design sweep): many independent mirrors of uneven polynomial
+ * degree and element count held by one context.  tn_batch_create(n) replaces
+ * any mesh of the context by n empty slots; tn_batch_set fills slot i with a
+ * mesh (as tn_build_mesh), its materials (as tn_set_materials) and its beam
+ * (as tn_set_beam).  Once every slot is set the context holds the batch:
+ *   - unknowns are concatenated mirror by mirror (each in the field layout
+ *     above); tn_batch_offsets gives the first unknown and the first layer of
+ *     every mirror (n + 1 entries each) and tn_ndof the total;
+ *   - tn_apply_operator applies the block-diagonal operator of all mirrors:
+ *     one launch per polynomial degree present, each CTA working on one
+ *     element of one mirror;
+ *   - tn_precond_apply (TN_PC_ZLINE only) and tn_solve solve all mirrors at
+ *     once (one Krylov iteration serves every mirror; the energy test covers
+ *     every layer of every mirror);
+ *   - tn_layer_energies returns the energies of all layers of all mirrors.
+ * tn_diagonal, TN_PC_JACOBI and tn_energy_grad need a single mesh. */
+tn_status tn_batch_create(tn_ctx *ctx, int n_instances);
+tn_status tn_batch_set(tn_ctx *ctx, int instance, const tn_mesh_desc *desc, int n_materials,
+                       const tn_material *m, double r0, double F0);
+tn_status tn_batch_offsets(const tn_ctx *ctx, int64_t *dof_off, int *layer_off);
+
 /* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
  * per layer, dissipated power 2 pi f sum_i phi_i U_i):
  *   S_out = 4 kB_T sum_i phi_i U_i / (pi f F0^2).  Host only. */

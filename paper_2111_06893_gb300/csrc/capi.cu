@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "tn_internal.h"
 #include "tn_precond.h"
@@ -42,8 +43,35 @@ void dfree(T *&p) {
 }
 }  // namespace
 
+// one mirror of a batch: its own mesh tables and material table on the device
+struct BatchInst {
+  tn::HostMesh hm;
+  DevMesh dm{};
+  double *colgeo = nullptr, *slabgeo = nullptr, *layer_c = nullptr;
+  float *colgeo32 = nullptr, *slabgeo32 = nullptr, *layer_c32 = nullptr;
+  int *colnb = nullptr, *colnbf = nullptr, *slab_layer = nullptr;
+  double r0 = 1.0, F0 = 1.0;
+  long long dof_off = 0, fac_off = 0;
+  int layer_off = 0;
+  bool set = false;
+};
+
+struct Batch {
+  int n = 0;
+  BatchInst *inst = nullptr;
+  bool ready = false;
+  long long ndof = 0, nfac = 0;
+  int n_layers = 0, n_elems = 0;
+  DevMesh *d_meshes = nullptr;
+  long long *d_dof_off = nullptr, *d_fac_off = nullptr;
+  int2 *d_work = nullptr, *d_lines = nullptr;
+  OpSys sys;
+  int2 *h_work = nullptr;  // (instance, element) in the order of the apply partials
+};
+
 struct tn_ctx {
   int device = 0;
+  Batch *batch = nullptr;
   cudaStream_t stream = nullptr;   // the caller's stream
   cudaStream_t sstream = nullptr;  // internal stream used for graph capture
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -91,6 +119,11 @@ static void free_precond(tn_ctx *c) {
   c->zready = false;
 }
 
+static OpSys make_sys(const tn_ctx *c);
+static int total_layers(const tn_ctx *c);
+static int apply_parts(const tn_ctx *c);
+static bool is_batch(const tn_ctx *c);
+
 static void free_mesh(tn_ctx *c) {
   free_precond(c);
   dfree(c->d_colgeo);
@@ -126,7 +159,8 @@ static void free_ws(tn_ctx *c) {
 }
 
 static tn_status ensure_ws(tn_ctx *c) {
-  if (c->ws_ndof == c->ndof && c->ws_E == (size_t)c->dm.E && c->ws_layers == c->dm.n_layers) return TN_OK;
+  const int E = apply_parts(c), NL = total_layers(c);
+  if (c->ws_ndof == c->ndof && c->ws_E == (size_t)E && c->ws_layers == NL) return TN_OK;
   free_ws(c);
   const size_t n = c->ndof;
   const size_t d8 = n * sizeof(double), f4 = n * sizeof(float);
@@ -136,12 +170,12 @@ static tn_status ensure_ws(tn_ctx *c) {
   A((void **)&c->r64, d8); A((void **)&c->z64, d8); A((void **)&c->p64, d8); A((void **)&c->q64, d8);
   A((void **)&c->dinv32, f4); A((void **)&c->b32, f4); A((void **)&c->r32, f4); A((void **)&c->z32, f4);
   A((void **)&c->p32, f4); A((void **)&c->q32, f4); A((void **)&c->d32, f4);
-  A((void **)&c->part_elem, sizeof(double) * c->dm.E);
+  A((void **)&c->part_elem, sizeof(double) * E);
   A((void **)&c->part_red, sizeof(double) * 2 * tn::reduction_blocks());
   A((void **)&c->sum_dev, sizeof(double) * 2);
   A((void **)&c->scal, sizeof(tn_pcg_scalars));
-  A((void **)&c->elem_energy, sizeof(double) * c->dm.E);
-  A((void **)&c->layer_energy, sizeof(double) * c->dm.n_layers);
+  A((void **)&c->elem_energy, sizeof(double) * E);
+  A((void **)&c->layer_energy, sizeof(double) * NL);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&c->scal_host, sizeof(tn_pcg_scalars));
   if (e != cudaSuccess) {
     free_ws(c);
@@ -149,8 +183,8 @@ static tn_status ensure_ws(tn_ctx *c) {
     return fail(TN_ENOMEM, "workspace allocation of %zu DOF failed: %s", n, cudaGetErrorString(e));
   }
   c->ws_ndof = n;
-  c->ws_E = c->dm.E;
-  c->ws_layers = c->dm.n_layers;
+  c->ws_E = E;
+  c->ws_layers = NL;
   return TN_OK;
 }
 
@@ -186,12 +220,25 @@ static tn_status ensure_fcg(tn_ctx *c, int m) {
 static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   if (c->zready) return TN_OK;
   free_precond(c);
-  const size_t bb = tn_zline_block_bytes(c->dm), fb = tn_zline_factor_bytes(c->dm);
+  size_t bb = 0, fb = 0;
+  int nparts = 0;
+  if (is_batch(c)) {
+    for (int i = 0; i < c->batch->n; ++i) {
+      const size_t b1 = tn_zline_block_bytes(c->batch->inst[i].dm);
+      bb = b1 > bb ? b1 : bb;
+    }
+    fb = (size_t)c->batch->nfac * sizeof(float);
+    nparts = c->batch->sys.n_rz_parts;
+  } else {
+    bb = tn_zline_block_bytes(c->dm);
+    fb = tn_zline_factor_bytes(c->dm);
+    nparts = tn_zline_partials(c->dm);
+  }
   double *blk = nullptr;
   cudaError_t e = cudaMalloc((void **)&blk, bb);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac, fb);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac64, 2 * fb);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zpart, sizeof(double) * tn_zline_partials(c->dm));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zpart, sizeof(double) * nparts);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->zstatus, sizeof(int));
   if (e != cudaSuccess) {
     if (blk) cudaFree(blk);
@@ -201,7 +248,14 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   }
   int status = 0;
   e = cudaMemsetAsync(c->zstatus, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = tn_zline_setup(c->dm, blk, c->zfac, c->zfac64, c->zstatus, st);
+  if (!is_batch(c)) {
+    if (e == cudaSuccess) e = tn_zline_setup(c->dm, blk, c->zfac, c->zfac64, c->zstatus, st);
+  } else {
+    for (int i = 0; i < c->batch->n && e == cudaSuccess; ++i) {
+      const BatchInst &q = c->batch->inst[i];
+      e = tn_zline_setup(q.dm, blk, c->zfac + q.fac_off, c->zfac64 + q.fac_off, c->zstatus, st);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->zstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(blk);
@@ -211,6 +265,38 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   return TN_OK;
 }
 
+// per-layer energies of u (all mirrors of a batch, concatenated) into host out
+static cudaError_t energies_host(tn_ctx *c, const double *u, double *out, cudaStream_t st) {
+  if (!is_batch(c)) {
+    cudaError_t e = tn_launch_energy(c->dm, u, c->elem_energy, c->layer_energy, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, c->layer_energy, sizeof(double) * c->dm.n_layers, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  }
+  Batch *b = c->batch;
+  const OpSys &s = b->sys;
+  cudaError_t e = cudaSuccess;
+  for (int g = 0; g < s.ngroups && e == cudaSuccess; ++g)
+    e = tn_launch_energy_batch(s.gN[g], b->d_meshes, s.gwork[g], s.gcount[g], b->d_dof_off, u,
+                               c->elem_energy + s.gpart_off[g], st);
+  double *tmp = (double *)std::malloc(sizeof(double) * b->n_elems);
+  if (!tmp) return cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, c->elem_energy, sizeof(double) * b->n_elems, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    for (int l = 0; l < b->n_layers; ++l) out[l] = 0.0;
+    // fixed order: the order of the work list
+    for (int w = 0; w < b->n_elems; ++w) {
+      const int2 it = b->h_work[w];
+      const BatchInst &q = b->inst[it.x];
+      out[q.layer_off + q.hm.slab_layer[it.y / q.hm.ncol]] += tmp[w];
+    }
+  }
+  std::free(tmp);
+  return e;
+}
+
 // energies of the current iterate and their largest relative change since the
 // previous call (for the energy stopping test)
 struct EnergyTrack {
@@ -218,16 +304,13 @@ struct EnergyTrack {
   const double *u;
   cudaStream_t st;
   double tol;
-  double prev[4096];
-  double cur[4096];
+  std::vector<double> prev = std::vector<double>(65536), cur = std::vector<double>(65536);
   bool have_prev = false;
   double change = INFINITY;
   cudaError_t err = cudaSuccess;
   bool step() {
-    const int nl = c->dm.n_layers;
-    err = tn_launch_energy(c->dm, u, c->elem_energy, c->layer_energy, st);
-    if (err == cudaSuccess) err = cudaMemcpyAsync(cur, c->layer_energy, sizeof(double) * nl, cudaMemcpyDeviceToHost, st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    const int nl = total_layers(c);
+    err = energies_host(c, u, cur.data(), st);
     if (err != cudaSuccess) return true;
     bool ok = have_prev;
     double ch = 0.0;
@@ -243,8 +326,53 @@ struct EnergyTrack {
   static bool hook(void *self) { return static_cast<EnergyTrack *>(self)->step(); }
 };
 
+static void free_batch(tn_ctx *c) {
+  Batch *b = c->batch;
+  if (!b) return;
+  for (int i = 0; i < b->n; ++i) {
+    BatchInst &q = b->inst[i];
+    dfree(q.colgeo); dfree(q.slabgeo); dfree(q.layer_c); dfree(q.colgeo32); dfree(q.slabgeo32);
+    dfree(q.layer_c32); dfree(q.colnb); dfree(q.colnbf); dfree(q.slab_layer);
+    tn::free_host_mesh(&q.hm);
+  }
+  delete[] b->inst;
+  dfree(b->d_meshes); dfree(b->d_dof_off); dfree(b->d_fac_off); dfree(b->d_work); dfree(b->d_lines);
+  delete[] b->h_work;
+  delete b;
+  c->batch = nullptr;
+}
+
+static bool is_batch(const tn_ctx *c) { return c->batch != nullptr; }
+
+static OpSys make_sys(const tn_ctx *c) {
+  if (is_batch(c)) return c->batch->sys;
+  OpSys s;
+  s.m = &c->dm;
+  s.n_apply_parts = c->dm.E;
+  s.n_rz_parts = tn_zline_partials(c->dm);
+  return s;
+}
+
+static int total_layers(const tn_ctx *c) { return is_batch(c) ? c->batch->n_layers : c->dm.n_layers; }
+static int apply_parts(const tn_ctx *c) { return is_batch(c) ? c->batch->n_elems : c->dm.E; }
+
+// b of every mirror (beam load)
+static cudaError_t make_rhs(const tn_ctx *c, double *b, cudaStream_t st) {
+  if (!is_batch(c)) return tn_launch_rhs(c->dm, c->r0, c->F0, b, st);
+  for (int i = 0; i < c->batch->n; ++i) {
+    const BatchInst &q = c->batch->inst[i];
+    cudaError_t e = tn_launch_rhs(q.dm, q.r0, q.F0, b + q.dof_off, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static tn_status need_ready(const tn_ctx *c, bool beam) {
   if (!c) return fail(TN_EINVAL, "null context");
+  if (c->batch) {
+    if (!c->batch->ready) return fail(TN_ESTATE, "batch not finalised: set every instance first");
+    return TN_OK;
+  }
   if (!c->have_mesh) return fail(TN_ESTATE, "no mesh: call tn_build_mesh first");
   if (!c->have_mat) return fail(TN_ESTATE, "no materials: call tn_set_materials after tn_build_mesh");
   if (beam && !c->have_beam) return fail(TN_ESTATE, "no beam: call tn_set_beam first");
@@ -293,6 +421,7 @@ void tn_destroy(tn_ctx *c) {
   cudaSetDevice(c->device);
   free_ws(c);
   free_mesh(c);
+  free_batch(c);
   dfree(c->d_layer_c);
   dfree(c->d_layer_c32);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -310,6 +439,7 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   CU_TRY(cudaStreamSynchronize(c->stream), "sync before rebuilding the mesh");
   free_mesh(c);
+  free_batch(c);
   free_ws(c);
   dfree(c->d_layer_c);
   dfree(c->d_layer_c32);
@@ -366,13 +496,40 @@ tn_status tn_build_mesh(tn_ctx *c, const tn_mesh_desc *d) {
 
 tn_status tn_ndof(const tn_ctx *c, int64_t *ndof) {
   if (!c || !ndof) return fail(TN_EINVAL, "null argument");
-  if (!c->have_mesh) return fail(TN_ESTATE, "no mesh");
+  if (c->batch ? !c->batch->ready : !c->have_mesh) return fail(TN_ESTATE, "no mesh");
   *ndof = (int64_t)c->ndof;
   return TN_OK;
 }
 
+// (c11, c12, c44) per layer from the ABI materials; false + message on error
+static bool material_table(int n, const tn_material *mats, double *h, char *msg, int len) {
+  for (int i = 0; i < n; ++i) {
+    const tn_material &m = mats[i];
+    if (m.kind == TN_ISO) {
+      if (!(m.Y > 0.0) || !(m.nu > -1.0 && m.nu < 0.5)) {
+        std::snprintf(msg, len, "material %d: need Y > 0 and -1 < nu < 1/2", i);
+        return false;
+      }
+      const double mu = m.Y / (2.0 * (1.0 + m.nu));
+      const double lam = m.Y * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+      h[3 * i] = lam + 2.0 * mu; h[3 * i + 1] = lam; h[3 * i + 2] = mu;
+    } else if (m.kind == TN_CUBIC) {
+      if (!(m.c44 > 0.0) || !(m.c11 > std::fabs(m.c12)) || !(m.c11 + 2.0 * m.c12 > 0.0)) {
+        std::snprintf(msg, len, "material %d: cubic stiffness not positive definite", i);
+        return false;
+      }
+      h[3 * i] = m.c11; h[3 * i + 1] = m.c12; h[3 * i + 2] = m.c44;
+    } else {
+      std::snprintf(msg, len, "material %d: unknown kind %d", i, m.kind);
+      return false;
+    }
+  }
+  return true;
+}
+
 tn_status tn_set_materials(tn_ctx *c, int n, const tn_material *mats) {
   if (!c || !mats) return fail(TN_EINVAL, "null argument");
+  if (c->batch) return fail(TN_ESTATE, "the context holds a batch: use tn_batch_set");
   if (!c->have_mesh) return fail(TN_ESTATE, "no mesh: call tn_build_mesh first");
   if (n != c->hm.n_layers) return fail(TN_EINVAL, "got %d materials for %d layers", n, c->hm.n_layers);
   double *h = (double *)std::malloc(sizeof(double) * 3 * n);
@@ -430,6 +587,163 @@ tn_status tn_set_beam(tn_ctx *c, double r0, double F0) {
   return TN_OK;
 }
 
+// ---------------------------------------------------------------- batches
+
+static tn_status batch_finalize(tn_ctx *c) {
+  Batch *b = c->batch;
+  long long dof = 0, fac = 0;
+  int lay = 0, elems = 0;
+  for (int i = 0; i < b->n; ++i) {
+    BatchInst &q = b->inst[i];
+    q.dof_off = dof;
+    q.fac_off = fac;
+    q.layer_off = lay;
+    const long long M = 3LL * q.hm.N;
+    dof += 3LL * q.hm.N * q.hm.N * q.hm.N * q.hm.E;
+    fac += (long long)tn_zline_factor_entries(q.dm);
+    (void)M;
+    lay += q.hm.n_layers;
+    elems += q.hm.E;
+  }
+  b->ndof = dof; b->nfac = fac; b->n_layers = lay; b->n_elems = elems;
+  std::vector<int2> work, lines;
+  OpSys &s = b->sys;
+  s = OpSys();
+  int rz = 0;
+  for (int N = TN_MIN_N; N <= TN_MAX_N; ++N) {
+    const int w0 = (int)work.size(), l0 = (int)lines.size();
+    for (int i = 0; i < b->n; ++i) {
+      const BatchInst &q = b->inst[i];
+      if (q.hm.N != N) continue;
+      for (int e = 0; e < q.hm.E; ++e) work.push_back(make_int2(i, e));
+      for (int l = 0; l < q.hm.ncol * N * N; ++l) lines.push_back(make_int2(i, l));
+    }
+    if ((int)work.size() == w0) continue;
+    const int g = s.ngroups++;
+    s.gN[g] = N;
+    s.gcount[g] = (int)work.size() - w0;
+    s.gpart_off[g] = w0;
+    s.glines[g] = (int)lines.size() - l0;
+    s.grz_off[g] = rz;
+    rz += (s.glines[g] + 3) / 4;
+    s.gwork[g] = reinterpret_cast<const int2 *>((size_t)w0);   // offsets, fixed below
+    s.gline[g] = reinterpret_cast<const int2 *>((size_t)l0);
+  }
+  std::vector<DevMesh> dms(b->n);
+  std::vector<long long> doff(b->n), foff(b->n);
+  for (int i = 0; i < b->n; ++i) { dms[i] = b->inst[i].dm; doff[i] = b->inst[i].dof_off; foff[i] = b->inst[i].fac_off; }
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void **dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up((void **)&b->d_meshes, dms.data(), sizeof(DevMesh) * b->n);
+  up((void **)&b->d_dof_off, doff.data(), sizeof(long long) * b->n);
+  up((void **)&b->d_fac_off, foff.data(), sizeof(long long) * b->n);
+  up((void **)&b->d_work, work.data(), sizeof(int2) * work.size());
+  up((void **)&b->d_lines, lines.data(), sizeof(int2) * lines.size());
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the batch");
+  for (int g = 0; g < s.ngroups; ++g) {
+    s.gwork[g] = b->d_work + (size_t)s.gwork[g];
+    s.gline[g] = b->d_lines + (size_t)s.gline[g];
+  }
+  s.meshes = b->d_meshes;
+  s.dof_off = b->d_dof_off;
+  s.fac_off = b->d_fac_off;
+  s.n_apply_parts = elems;
+  s.n_rz_parts = rz;
+  b->h_work = new (std::nothrow) int2[work.size()];
+  if (!b->h_work) return fail(TN_ENOMEM, "host allocation failed");
+  std::memcpy(b->h_work, work.data(), sizeof(int2) * work.size());
+  c->ndof = (size_t)dof;
+  b->ready = true;
+  return TN_OK;
+}
+
+extern "C" {
+
+tn_status tn_batch_create(tn_ctx *c, int n) {
+  if (!c) return fail(TN_EINVAL, "null context");
+  if (n < 1 || n > 65536) return fail(TN_EINVAL, "need 1 <= n <= 65536 instances");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  CU_TRY(cudaStreamSynchronize(c->stream), "sync before replacing the mesh");
+  free_mesh(c);
+  free_batch(c);
+  free_ws(c);
+  dfree(c->d_layer_c);
+  dfree(c->d_layer_c32);
+  c->have_mat = false;
+  Batch *b = new (std::nothrow) Batch();
+  if (b) b->inst = new (std::nothrow) BatchInst[n];
+  if (!b || !b->inst) { delete b; return fail(TN_ENOMEM, "host allocation failed"); }
+  b->n = n;
+  c->batch = b;
+  c->ndof = 0;
+  return TN_OK;
+}
+
+tn_status tn_batch_set(tn_ctx *c, int i, const tn_mesh_desc *d, int n_mat, const tn_material *mats, double r0,
+                       double F0) {
+  if (!c || !d || !mats) return fail(TN_EINVAL, "null argument");
+  if (!c->batch) return fail(TN_ESTATE, "no batch: call tn_batch_create first");
+  Batch *b = c->batch;
+  if (i < 0 || i >= b->n) return fail(TN_EINVAL, "instance %d out of range", i);
+  if (b->inst[i].set) return fail(TN_ESTATE, "instance %d already set", i);
+  if (!(r0 > 0.0) || !std::isfinite(F0)) return fail(TN_EINVAL, "need r0 > 0 and finite F0");
+  tn::HostMesh hm;
+  char msg[256] = "";
+  tn_status st = tn::build_host_mesh(d, &hm, msg, sizeof(msg));
+  if (st != TN_OK) return fail(st, "instance %d: %s", i, msg);
+  if (n_mat != hm.n_layers) { tn::free_host_mesh(&hm); return fail(TN_EINVAL, "instance %d: %d materials for %d layers", i, n_mat, hm.n_layers); }
+  std::vector<double> h(3 * n_mat);
+  if (!material_table(n_mat, mats, h.data(), msg, sizeof(msg))) { tn::free_host_mesh(&hm); return fail(TN_EINVAL, "instance %d: %s", i, msg); }
+  std::vector<float> h32(h.begin(), h.end());
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  BatchInst &q = b->inst[i];
+  q.hm = hm;
+  const int N2 = hm.N * hm.N;
+  const size_t ncg = (size_t)hm.ncol * CG_NF * N2, nsg = (size_t)hm.nslab * SG_NF * hm.N;
+  std::vector<float> cg32(hm.colgeo, hm.colgeo + ncg), sg32(hm.slabgeo, hm.slabgeo + nsg);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void **dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up((void **)&q.colgeo, hm.colgeo, sizeof(double) * ncg);
+  up((void **)&q.slabgeo, hm.slabgeo, sizeof(double) * nsg);
+  up((void **)&q.colgeo32, cg32.data(), sizeof(float) * ncg);
+  up((void **)&q.slabgeo32, sg32.data(), sizeof(float) * nsg);
+  up((void **)&q.colnb, hm.colnb, sizeof(int) * 4 * hm.ncol);
+  up((void **)&q.colnbf, hm.colnbf, sizeof(int) * 4 * hm.ncol);
+  up((void **)&q.slab_layer, hm.slab_layer, sizeof(int) * hm.nslab);
+  up((void **)&q.layer_c, h.data(), sizeof(double) * h.size());
+  up((void **)&q.layer_c32, h32.data(), sizeof(float) * h32.size());
+  if (e != cudaSuccess) return cuda_fail(e, "uploading a batch instance");
+  DevMesh &m = q.dm;
+  m.N = hm.N; m.p = hm.p; m.E = hm.E; m.ncol = hm.ncol; m.nslab = hm.nslab; m.n_layers = hm.n_layers;
+  m.bc_side = hm.bc_side; m.bc_bottom = hm.bc_bottom; m.penC = hm.penC; m.penC32 = (float)hm.penC;
+  m.colgeo = q.colgeo; m.slabgeo = q.slabgeo; m.colnb = q.colnb; m.colnbf = q.colnbf; m.slab_layer = q.slab_layer;
+  m.layer_c = q.layer_c; m.colgeo32 = q.colgeo32; m.slabgeo32 = q.slabgeo32; m.layer_c32 = q.layer_c32;
+  q.r0 = r0;
+  q.F0 = F0;
+  q.set = true;
+  for (int k = 0; k < b->n; ++k)
+    if (!b->inst[k].set) return TN_OK;
+  return batch_finalize(c);
+}
+
+tn_status tn_batch_offsets(const tn_ctx *c, int64_t *dof_off, int *layer_off) {
+  if (!c || !dof_off || !layer_off) return fail(TN_EINVAL, "null argument");
+  if (!c->batch || !c->batch->ready) return fail(TN_ESTATE, "no finalised batch");
+  const Batch *b = c->batch;
+  for (int i = 0; i < b->n; ++i) { dof_off[i] = b->inst[i].dof_off; layer_off[i] = b->inst[i].layer_off; }
+  dof_off[b->n] = b->ndof;
+  layer_off[b->n] = b->n_layers;
+  return TN_OK;
+}
+
+}  // extern "C"
+
 static tn_status check_buf(const tn_ctx *c, const void *p, size_t elem, const char *name) {
   if (!p) return fail(TN_EINVAL, "%s is null", name);
   if (((uintptr_t)p) % 16) return fail(TN_EINVAL, "%s must be 16-byte aligned", name);
@@ -447,7 +761,7 @@ tn_status tn_apply_operator(tn_ctx *c, int precision, const void *u, void *y) {
   const char *a = (const char *)u, *b = (const char *)y;
   const size_t bytes = c->ndof * es;
   if (a < b + bytes && b < a + bytes) return fail(TN_EINVAL, "u and y overlap");
-  CU_TRY(tn_launch_apply(c->dm, precision, u, y, nullptr, nullptr, c->stream), "apply launch");
+  CU_TRY(make_sys(c).apply(precision, u, y, nullptr, c->stream), "apply launch");
   return TN_OK;
 }
 
@@ -455,13 +769,14 @@ tn_status tn_rhs(tn_ctx *c, double *b) {
   tn_status st = need_ready(c, true);
   if (st) return st;
   if ((st = check_buf(c, b, 8, "b"))) return st;
-  CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, b, c->stream), "rhs launch");
+  CU_TRY(make_rhs(c, b, c->stream), "rhs launch");
   return TN_OK;
 }
 
 tn_status tn_diagonal(tn_ctx *c, double *d) {
   tn_status st = need_ready(c, false);
   if (st) return st;
+  if (is_batch(c)) return fail(TN_EINVAL, "tn_diagonal works on a single mesh");
   if ((st = check_buf(c, d, 8, "d"))) return st;
   CU_TRY(tn_launch_diag(c->dm, d, c->stream), "diag launch");
   return TN_OK;
@@ -484,10 +799,11 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if ((st = check_buf(c, u, 8, "u"))) return st;
   if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
   if (o->precond != TN_PC_JACOBI && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "unknown preconditioner");
+  if (is_batch(c) && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "a batch is solved with TN_PC_ZLINE");
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
   if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
   if (!(o->energy_rtol >= 0.0)) return fail(TN_EINVAL, "energy_rtol must be >= 0");
-  if (c->hm.n_layers > 4096) return fail(TN_EINVAL, "at most 4096 layers");
+  if (total_layers(c) > 65536) return fail(TN_EINVAL, "at most 65536 layers in all");
   if (o->mode == TN_SOLVE_MIXED_F32 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0) || o->max_outer < 1))
     return fail(TN_EINVAL, "mixed mode needs 0 < inner_rtol < 1 and max_outer >= 1");
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
@@ -499,9 +815,10 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   CU_TRY(cudaEventRecord(c->ev_in, c->stream), "event");
   CU_TRY(cudaStreamWaitEvent(s, c->ev_in, 0), "event wait");
   const size_t n = c->ndof;
+  const OpSys sys = make_sys(c);
   if (rhs) CU_TRY(cudaMemcpyAsync(c->b64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "rhs copy");
-  else CU_TRY(tn_launch_rhs(c->dm, c->r0, c->F0, c->b64, s), "rhs");
-  CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
+  else CU_TRY(make_rhs(c, c->b64, s), "rhs");
+  if (!is_batch(c)) CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
   double bb = 0.0;
   CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
   const bool zl = o->precond == TN_PC_ZLINE;
@@ -514,7 +831,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (bb == 0.0) {
     CU_TRY(tn::fill_f64(n, u, 0.0, s), "zero");
   } else if (o->mode == TN_SOLVE_F64) {
-    CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv64, TN_F64, s), "dinv");
+    if (!is_batch(c)) CU_TRY(tn::pcg_setup_dinv(n, c->diag64, c->dinv64, TN_F64, s), "dinv");
     PcgVectors v{u, c->r64, c->z64, c->p64, c->q64, c->b64, c->dinv64};
     if (zl) { v.zfac = c->zfac64; v.part_rz = c->zpart; }
     // FP64 PCG; restarted from the current iterate (true residual) if the
@@ -526,7 +843,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
     bool energy_done = false;
     for (int restart = 0; restart < 4 && !energy_done; ++restart) {
       int applies = 0;
-      CU_TRY(tn::pcg_f64(c->dm, n, v, x0_zero, o->rtol, o->max_iter - r.inner_iters, chunk, c->scal,
+      CU_TRY(tn::pcg_f64(sys, n, v, x0_zero, o->rtol, o->max_iter - r.inner_iters, chunk, c->scal,
                          c->scal_host, c->part_elem, c->part_red, s, &applies, hook), "pcg f64");
       CU_TRY(et.err, "energy check");
       energy_done = o->energy_rtol > 0.0 && et.have_prev && et.change <= o->energy_rtol;
@@ -539,14 +856,14 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
         break;
       }
       double rr = 0.0;
-      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
+      CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
       r.applies_f64 += 1;
       if (energy_done || std::sqrt(rr / bb) <= o->rtol || r.inner_iters >= o->max_iter) break;
       x0_zero = false;
     }
     r.status = energy_done ? 1 : 0;
   } else {
-    CU_TRY(tn::pcg_setup_dinv(c->dm, n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
+    if (!is_batch(c)) CU_TRY(tn::pcg_setup_dinv(n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
     const int m = o->fcg_window > 0 ? (o->fcg_window > 16 ? 16 : o->fcg_window) : 8;
     const int kin = o->inner_max > 0 ? o->inner_max : 30;
     if ((st = ensure_fcg(c, m))) return st;
@@ -557,7 +874,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       CU_TRY(cudaMemcpyAsync(c->r64, c->b64, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "r = b");
     } else {
       double rr0;
-      CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr0, s), "residual");
+      CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr0, s), "residual");
       r.applies_f64 += 1;
     }
     int total_inner = 0;
@@ -586,14 +903,14 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       PcgVectors v{c->d32, c->r32, c->z32, c->p32, c->q32, c->b32, c->dinv32};
       if (zl) { v.zfac = c->zfac; v.part_rz = c->zpart; }
       int applies = 0;
-      CU_TRY(tn::pcg_f32(c->dm, n, v, true, o->inner_rtol, kin, kin, c->scal, c->scal_host, c->part_elem,
+      CU_TRY(tn::pcg_f32(sys, n, v, true, o->inner_rtol, kin, kin, c->scal, c->scal_host, c->part_elem,
                          c->part_red, s, &applies), "pcg f32");
       total_inner += c->scal_host->iters;
       r.applies_f32 += applies;
       r.outer_iters += 1;
       // z = |r| d (FP64), q = A z
       CU_TRY(tn::upcast(n, c->d32, rn, c->z64, s), "upcast");
-      CU_TRY(tn_launch_apply(c->dm, TN_F64, c->z64, c->q64, nullptr, nullptr, s), "apply f64");
+      CU_TRY(sys.apply(TN_F64, c->z64, c->q64, nullptr, s), "apply f64");
       tn::g_launches += 1;
       r.applies_f64 += 1;
       // keep the new direction A-orthogonal to the last nb ones
@@ -623,7 +940,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   r.status = 0;
   if (bb != 0.0 && result == TN_OK) {
     double rr = 0.0;
-    CU_TRY(tn::residual_f64(c->dm, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
+    CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
     r.applies_f64 += 1;
     r.rel_residual = std::sqrt(rr / bb);
     if (!(r.rel_residual <= o->rtol) && !energy_ok)
@@ -654,10 +971,11 @@ tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r,
   if ((st = ensure_ws(c))) return st;
   if (precond == TN_PC_ZLINE) {
     if ((st = ensure_zline(c, c->stream))) return st;
-    CU_TRY(tn_zline_solve(c->dm, precision, precision == TN_F64 ? (const void *)c->zfac64 : (const void *)c->zfac,
-                          r, z, c->zpart, nullptr, c->stream), "z-line solve");
+    CU_TRY(make_sys(c).zsolve(precision, precision == TN_F64 ? (const void *)c->zfac64 : (const void *)c->zfac,
+                              r, z, c->zpart, nullptr, c->stream), "z-line solve");
     return TN_OK;
   }
+  if (is_batch(c)) return fail(TN_EINVAL, "Jacobi needs a single mesh");
   CU_TRY(tn_launch_diag(c->dm, c->diag64, c->stream), "diag");
   CU_TRY(tn_jacobi_apply(c->ndof, precision, c->diag64, r, z, c->stream), "jacobi");
   return TN_OK;
@@ -704,6 +1022,7 @@ tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, con
   tn_status st = need_ready(c, true);
   if (st) return st;
   if (!o || !w_host || !dJ_dslab_z || !dJ_dr0 || !dJ_dmat) return fail(TN_EINVAL, "null argument");
+  if (is_batch(c)) return fail(TN_EINVAL, "tn_energy_grad works on a single mesh");
   if ((st = check_buf(c, u, 8, "u"))) return st;
   if (lambda && (st = check_buf(c, lambda, 8, "lambda"))) return st;
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
@@ -802,10 +1121,7 @@ tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {
   if (!U_host) return fail(TN_EINVAL, "U_host is null");
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   if ((st = ensure_ws(c))) return st;
-  CU_TRY(tn_launch_energy(c->dm, u, c->elem_energy, c->layer_energy, c->stream), "energy launch");
-  CU_TRY(cudaMemcpyAsync(U_host, c->layer_energy, sizeof(double) * c->dm.n_layers, cudaMemcpyDeviceToHost,
-                         c->stream), "energy copy");
-  CU_TRY(cudaStreamSynchronize(c->stream), "energy sync");
+  CU_TRY(energies_host(c, u, U_host, c->stream), "energies");
   return TN_OK;
 }
 

@@ -557,11 +557,12 @@ __device__ __forceinline__ int line_node(int d, int l, int a) {
   return (a * N + hi) * N + lo;               // (j, i) fixed, k = a
 }
 
+// u, y: the element's instance vectors; partial: this CTA's slot or nullptr
 template <int N, typename T>
-__global__ void __launch_bounds__(nthreads<N>())
-apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+__device__ __forceinline__ void apply2_body(const DevMesh &m, const int e, const T *__restrict__ u,
+                                            T *__restrict__ y, double *__restrict__ partial,
+                                            unsigned char *smem_raw) {
   constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *su = reinterpret_cast<T *>(smem_raw);  // [3][n]
   T *sG = su + 3 * n;                        // [3 dir][3 comp][n] logical gradient, then fluxes F^m_j
   T *sY = sG + 9 * n;                        // [3 dir][3 comp][n] divergence partial sums
@@ -573,7 +574,7 @@ apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ 
   __shared__ T nbc[6][3];
   __shared__ double red[NT / 32];
 
-  const int e = e0 + blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int s = e / m.ncol, c = e - s * m.ncol;
   const T *ue = u + (size_t)e * 3 * n;
   for (int t = tid; t < 3 * n; t += NT) su[t] = ue[t];
@@ -847,9 +848,50 @@ apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ 
     if (tid == 0) {
       double sum = 0.0;
       for (int w = 0; w < NT / 32; ++w) sum += red[w];
-      partial[blockIdx.x] = sum;
+      *partial = sum;
     }
   }
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(nthreads<N>())
+apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  apply2_body<N, T>(m, e0 + blockIdx.x, u, y, partial ? partial + blockIdx.x : nullptr, smem_raw);
+}
+
+// a batch of meshes: CTA b works on element work[b].y of instance work[b].x
+template <int N, typename T>
+__global__ void __launch_bounds__(nthreads<N>())
+apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work,
+                    const long long *__restrict__ dof_off, const T *__restrict__ u, T *__restrict__ y,
+                    double *__restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) unsigned char sm_raw[sizeof(DevMesh)];
+  DevMesh &sm = *reinterpret_cast<DevMesh *>(sm_raw);
+  const int2 w = work[blockIdx.x];
+  if (threadIdx.x == 0) memcpy(sm_raw, &meshes[w.x], sizeof(DevMesh));
+  __syncthreads();
+  const long long off = dof_off[w.x];
+  apply2_body<N, T>(sm, w.y, u + off, y + off, partial ? partial + blockIdx.x : nullptr, smem_raw);
+}
+
+template <int N, typename T>
+cudaError_t launch_apply2_batch(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
+                                const T *u, T *y, double *partial, cudaStream_t st) {
+  constexpr size_t sm = apply2_smem<N, T>();
+  static int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t err = cudaFuncSetAttribute(apply2_batch_kernel<N, T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    configured_device = dev;
+  }
+  if (nwork <= 0) return cudaSuccess;
+  apply2_batch_kernel<N, T><<<nwork, nthreads<N>(), sm, st>>>(meshes, work, dof_off, u, y, partial);
+  return cudaGetLastError();
 }
 
 template <int N, typename T>
@@ -1090,6 +1132,64 @@ energy_kernel(const DevMesh m, int e0, const double *__restrict__ u, const doubl
   }
 }
 
+// element energies of a batch: out[b] = energy of element work[b].y of
+// instance work[b].x (FP64)
+template <int N>
+__global__ void __launch_bounds__(nthreads<N>())
+energy_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work,
+                    const long long *__restrict__ dof_off, const double *__restrict__ u, double *__restrict__ out) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  __shared__ double su[3 * n];
+  __shared__ double red[NT / 32];
+  __shared__ __align__(16) unsigned char m_raw[sizeof(DevMesh)];
+  DevMesh &m = *reinterpret_cast<DevMesh *>(m_raw);
+  const int2 w = work[blockIdx.x];
+  const int tid = threadIdx.x;
+  if (tid == 0) memcpy(m_raw, &meshes[w.x], sizeof(DevMesh));
+  __syncthreads();
+  const int e = w.y;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  const double *ue = u + dof_off[w.x] + (size_t)e * 3 * n;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = ue[t];
+  __syncthreads();
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const int L = m.slab_layer[s];
+  const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
+  double en = 0.0;
+  if (tid < n) {
+    const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
+    double dxi[3], deta[3], dzeta[3];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double *v = su + cc * n;
+      double a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a0 += Tab<double>::D(N, i, mm) * v[(k * N + j) * N + mm];
+        a1 += Tab<double>::D(N, j, mm) * v[(k * N + mm) * N + i];
+        a2 += Tab<double>::D(N, k, mm) * v[(mm * N + j) * N + i];
+      }
+      dxi[cc] = a0; deta[cc] = a1; dzeta[cc] = a2;
+    }
+    const int q = j * N + i;
+    const double dz = m.slabgeo[((size_t)s * SG_NF + SG_DZ) * N + k];
+    const Sym<double> S = strain<double>(dxi, deta, dzeta, cg[CG_IXX * N2 + q], cg[CG_IXY * N2 + q],
+                                         cg[CG_IEX * N2 + q], cg[CG_IEY * N2 + q], 1.0 / dz);
+    const Sym<double> sg2 = stress(S, c11, c12, c44);
+    const double dens = S.xx * sg2.xx + S.yy * sg2.yy + S.zz * sg2.zz +
+                        2.0 * (S.xy * sg2.xy + S.xz * sg2.xz + S.yz * sg2.yz);
+    en = 0.5 * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) * cg[CG_DET * N2 + q] * dz * dens;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
+  if ((tid & 31) == 0) red[tid >> 5] = en;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int ww = 0; ww < NT / 32; ++ww) sum += red[ww];
+    out[blockIdx.x] = sum;
+  }
+}
+
 // g_e = w[layer(e)] K_e u: the weak divergence of w detJ Y : sym grad u
 // (the volume part of the operator, no faces) -- d(sum_i w_i U_i)/du
 template <int N>
@@ -1290,4 +1390,35 @@ cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const doub
                               int nparts, cudaStream_t st) {
   rhs_dr0_kernel<<<nparts, 256, 0, st>>>(m, r0, F0, lam, part);
   return cudaGetLastError();
+}
+
+cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
+                                  const long long *dof_off, const void *u, void *y, double *partial,
+                                  cudaStream_t st) {
+  switch (N) {
+#define TN_CASE(NN)                                                                                    \
+  case NN:                                                                                            \
+    return precision == TN_F64                                                                        \
+               ? launch_apply2_batch<NN, double>(meshes, work, nwork, dof_off, (const double *)u,    \
+                                                 (double *)y, partial, st)                            \
+               : launch_apply2_batch<NN, float>(meshes, work, nwork, dof_off, (const float *)u,      \
+                                                (float *)y, partial, st);
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tn_launch_energy_batch(int N, const DevMesh *meshes, const int2 *work, int nwork,
+                                   const long long *dof_off, const double *u, double *out, cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  switch (N) {
+#define TN_CASE(NN)                                                                                    \
+  case NN:                                                                                            \
+    energy_batch_kernel<NN><<<nwork, nthreads<NN>(), 0, st>>>(meshes, work, dof_off, u, out);          \
+    return cudaGetLastError();
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+    default: return cudaErrorInvalidValue;
+  }
 }

@@ -29,6 +29,10 @@ cudaError_t tn_upload_lgl_precond(const LglTables *t) {
 
 namespace {
 
+// factor blocks are padded to a multiple of 4 entries (16-byte aligned for
+// cp.async of float and double blocks)
+__host__ __device__ constexpr int zpad(int M) { return ((M * M + 3) / 4) * 4; }
+
 #define LD(a, b) c_lgl_pc.D[N][(a) * N + (b)]
 #define LW(a) c_lgl_pc.w[N][(a)]
 
@@ -258,16 +262,27 @@ __global__ void zline_factor_kernel(int nlines, int S, double *__restrict__ blk,
         Dm[r * M + col] = w / dgl;
       }
     }
-    float *Lf = fac + (((size_t)line * S + s) * 2 + 0) * M * M;
-    double *Ld = fac64 + (((size_t)line * S + s) * 2 + 0) * M * M;
-    for (int col = 0; col < M; ++col)
+    // inverse of the lower-triangular factor (forward substitution on the
+    // identity), stored column-major; Z_s row-major; blocks padded to MP
+    constexpr int MP = zpad(M);
+    float *Lf = fac + (((size_t)line * S + s) * 2 + 0) * MP;
+    double *Ld = fac64 + (((size_t)line * S + s) * 2 + 0) * MP;
+    for (int col = 0; col < M; ++col) {
       for (int r = 0; r < M; ++r) {
-        const double v = r < col ? 0.0 : (r == col ? 1.0 / Dm[r * M + col] : Dm[r * M + col]);
-        Lf[col * M + r] = (float)v;
+        double v;
+        if (r < col) v = 0.0;
+        else if (r == col) v = 1.0 / Dm[r * M + r];
+        else {
+          double acc = 0.0;
+          for (int q = col; q < r; ++q) acc += Dm[r * M + q] * Ld[col * M + q];
+          v = -acc / Dm[r * M + r];
+        }
         Ld[col * M + r] = v;
+        Lf[col * M + r] = (float)v;
       }
-    float *Zf = fac + (((size_t)line * S + s) * 2 + 1) * M * M;
-    double *Zd = fac64 + (((size_t)line * S + s) * 2 + 1) * M * M;
+    }
+    float *Zf = fac + (((size_t)line * S + s) * 2 + 1) * MP;
+    double *Zd = fac64 + (((size_t)line * S + s) * 2 + 1) * MP;
     if (s > 0) {
       const double *Z = blk + (((size_t)line * S + s - 1) * 2 + 1) * M * M;
       for (int q = 0; q < M * M; ++q) { Zf[q] = (float)Z[q]; Zd[q] = Z[q]; }
@@ -277,85 +292,154 @@ __global__ void zline_factor_kernel(int nlines, int S, double *__restrict__ blk,
   }
 }
 
-// z = A_LL^{-1} r on every line; one warp per line, lane l = a * N + k.
-// Partial sums of r . z per block.
+// cp.async of one padded block pair (2 MP entries) into shared memory by a warp
+template <typename F, int MP>
+__device__ __forceinline__ void stage_pair(F *dst, const F *src, int lane) {
+  constexpr int CH = (2 * MP * (int)sizeof(F)) / 16;  // 16-byte chunks
+  const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+  for (int t = lane; t < CH; t += 32)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * t), "l"(src + t * (16 / (int)sizeof(F))));
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+__device__ __forceinline__ void wait_staged_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void wait_staged_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// z = A_LL^{-1} r on one line (one warp; lane l = a * N + k holds one unknown
+// of a slab).  Forward:  y_s = Linv_s (r_s - Z_s^T y_{s-1});
+// backward:  x_s = Linv_s^T (y_s - Z_{s+1} x_{s+1}).  Every product is a
+// broadcast matrix-vector product (no dependent substitution chain); the
+// slab's blocks are staged in shared memory (two buffers, cp.async) so that
+// global reads are contiguous.  Returns this lane's share of r . z.
 template <int N, typename T, typename F>
-__global__ void __launch_bounds__(128)
-zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, const T *__restrict__ r, T *__restrict__ z,
-                   double *__restrict__ part, const int *__restrict__ done) {
-  constexpr int M = 3 * N, N2 = N * N, n = N * N * N;
-  if (done && *done) return;
-  __shared__ double red[4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int line = blockIdx.x * 4 + warp;
-  const int nlines = m.ncol * N2;
+__device__ __forceinline__ T zline_line(const DevMesh &m, const F *__restrict__ fac, const T *__restrict__ r,
+                                        T *__restrict__ z, int line, int lane, F *buf) {
+  constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MP = zpad(M);
   const int S = m.nslab;
   T rzt = T(0);
-  if (line < nlines) {
-    const int c = line / N2, q = line - c * N2, i = q % N, j = q / N;
-    const int a = lane / N, k = lane - (lane / N) * N;
-    const bool act = lane < M;
-    const size_t off = (size_t)k * N2 + j * N + i;
-    T yprev = T(0);
-    for (int s = 0; s < S; ++s) {
-      const size_t e = (size_t)s * m.ncol + c;
-      const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
-      T b = act ? r[idx] : T(0);
-      const F *Lf = fac + (((size_t)line * S + s) * 2 + 0) * M * M;
-      const F *Zf = fac + (((size_t)line * S + s) * 2 + 1) * M * M;
-      if (s > 0) {  // b -= Z_s^T y_{s-1}
-#pragma unroll
-        for (int mm = 0; mm < M; ++mm) {
-          const T ym = __shfl_sync(0xffffffffu, yprev, mm);
-          if (act) b -= (T)Zf[mm * M + lane] * ym;
-        }
-      }
-      // L y = b, column by column
-      T y = T(0);
-#pragma unroll
-      for (int col = 0; col < M; ++col) {
-        const T yc = __shfl_sync(0xffffffffu, b, col) * (T)Lf[col * M + col];
-        if (lane == col) y = yc;
-        if (act && lane > col) b -= (T)Lf[col * M + lane] * yc;
-      }
-      if (act) z[idx] = y;
-      yprev = y;
+  const int c = line / N2, q = line - c * N2, i = q % N, j = q / N;
+  const int a = lane / N, k = lane - (lane / N) * N;
+  const bool act = lane < M;
+  const int ll = act ? lane : 0;
+  const size_t off = (size_t)k * N2 + j * N + i;
+  const F *base = fac + (size_t)line * S * 2 * MP;  // slab s: [Linv_s | Z_s]
+  // forward sweep
+  stage_pair<F, MP>(buf, base, lane);
+  T yprev = T(0);
+  for (int s = 0; s < S; ++s) {
+    F *cur = buf + (s & 1) * 2 * MP;
+    if (s + 1 < S) {
+      stage_pair<F, MP>(buf + ((s + 1) & 1) * 2 * MP, base + (size_t)(s + 1) * 2 * MP, lane);
+      wait_staged_all_but_one();
+    } else {
+      wait_staged_all();
     }
-    T xn = T(0);
-    for (int s = S - 1; s >= 0; --s) {
-      const size_t e = (size_t)s * m.ncol + c;
-      const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
-      T yv = act ? z[idx] : T(0);
-      const F *Lf = fac + (((size_t)line * S + s) * 2 + 0) * M * M;
-      if (s < S - 1) {  // yv -= Z_{s+1} x_{s+1}
-        const F *Zn = fac + (((size_t)line * S + s + 1) * 2 + 1) * M * M;
+    __syncwarp();
+    const F *Li = cur, *Zs = cur + MP;
+    const size_t e = (size_t)s * m.ncol + c;
+    const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
+    T b = act ? r[idx] : T(0);
+    if (s > 0) {
 #pragma unroll
-        for (int mm = 0; mm < M; ++mm) {
-          const T xm = __shfl_sync(0xffffffffu, xn, mm);
-          if (act) yv -= (T)Zn[lane * M + mm] * xm;
-        }
-      }
-      // L^T x = yv, from the last column
-      T x = T(0);
-#pragma unroll
-      for (int col = M - 1; col >= 0; --col) {
-        const T xc = __shfl_sync(0xffffffffu, yv, col) * (T)Lf[col * M + col];
-        if (lane == col) x = xc;
-        if (act && lane < col) yv -= (T)Lf[lane * M + col] * xc;
-      }
-      if (act) {
-        z[idx] = x;
-        rzt += r[idx] * x;
-      }
-      xn = x;
+      for (int cc = 0; cc < M; ++cc) b -= (T)Zs[cc * M + ll] * __shfl_sync(0xffffffffu, yprev, cc);
     }
+    T y = T(0);
+#pragma unroll
+    for (int cc = 0; cc < M; ++cc) y += (T)Li[cc * M + ll] * __shfl_sync(0xffffffffu, b, cc);
+    if (!act) y = T(0);
+    if (act) z[idx] = y;
+    yprev = y;
+    __syncwarp();  // buffer (s & 1) is restaged two slabs later
   }
-  double rz = (double)rzt;
+  // backward sweep: slab s needs Linv_s and Z_{s+1}
+  T xn = T(0);
+  for (int s = S - 1; s >= 0; --s) {
+    const F *Li = base + (size_t)s * 2 * MP;
+    F *cur = buf;
+    // stage Linv_s (first half of pair s) and Z_{s+1} (second half of pair s+1)
+    {
+      constexpr int CH = (MP * (int)sizeof(F)) / 16;
+      const unsigned d0 = (unsigned)__cvta_generic_to_shared(cur);
+      const unsigned d1 = (unsigned)__cvta_generic_to_shared(cur + MP);
+      for (int t = lane; t < CH; t += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d0 + 16 * t), "l"(Li + t * (16 / (int)sizeof(F))));
+      if (s + 1 < S) {
+        const F *Zn = base + (size_t)(s + 1) * 2 * MP + MP;
+        for (int t = lane; t < CH; t += 32)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d1 + 16 * t), "l"(Zn + t * (16 / (int)sizeof(F))));
+      }
+      asm volatile("cp.async.commit_group;\n" ::);
+      wait_staged_all();
+    }
+    __syncwarp();
+    const size_t e = (size_t)s * m.ncol + c;
+    const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
+    T yv = act ? z[idx] : T(0);
+    if (s < S - 1) {
+      const F *Zs = cur + MP;
+#pragma unroll
+      for (int cc = 0; cc < M; ++cc) yv -= (T)Zs[ll * M + cc] * __shfl_sync(0xffffffffu, xn, cc);
+    }
+    T x = T(0);
+#pragma unroll
+    for (int cc = 0; cc < M; ++cc) x += (T)cur[ll * M + cc] * __shfl_sync(0xffffffffu, yv, cc);
+    if (!act) x = T(0);
+    if (act) {
+      z[idx] = x;
+      rzt += r[idx] * x;
+    }
+    xn = x;
+    __syncwarp();
+  }
+  return rzt;
+}
+
+// four lines (warps) per block; partial sums of r . z per block
+__device__ __forceinline__ void block_partial_rz(double rz, double *part) {
+  __shared__ double red[4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
   if (lane == 0) red[warp] = rz;
   __syncthreads();
   if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+}
+
+template <int N, typename F>
+constexpr size_t zline_smem() { return sizeof(F) * 4 * 2 * 2 * zpad(3 * N); }
+
+template <int N, typename T, typename F>
+__global__ void __launch_bounds__(128)
+zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, const T *__restrict__ r, T *__restrict__ z,
+                   double *__restrict__ part, const int *__restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char zsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  F *buf = reinterpret_cast<F *>(zsm) + warp * 4 * zpad(3 * N);
+  const int line = blockIdx.x * 4 + warp;
+  T rzt = T(0);
+  if (line < m.ncol * N * N) rzt = zline_line<N, T, F>(m, fac, r, z, line, lane, buf);
+  block_partial_rz((double)rzt, part);
+}
+
+// a batch: warp w of block b handles line work[4 b + w] = (instance, line)
+template <int N, typename T, typename F>
+__global__ void __launch_bounds__(128)
+zline_solve_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work, int nwork,
+                         const long long *__restrict__ fac_off, const long long *__restrict__ dof_off,
+                         const F *__restrict__ fac, const T *__restrict__ r, T *__restrict__ z,
+                         double *__restrict__ part, const int *__restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char zsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  F *buf = reinterpret_cast<F *>(zsm) + warp * 4 * zpad(3 * N);
+  const int wi = blockIdx.x * 4 + warp;
+  T rzt = T(0);
+  if (wi < nwork) {
+    const int2 w = work[wi];
+    const long long off = dof_off[w.x];
+    rzt = zline_line<N, T, F>(meshes[w.x], fac + fac_off[w.x], r + off, z + off, w.y, lane, buf);
+  }
+  block_partial_rz((double)rzt, part);
 }
 
 template <int N>
@@ -374,11 +458,11 @@ cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, const void *r, 
   const int nlines = m.ncol * N * N;
   const int blocks = (nlines + 3) / 4;
   if (prec == TN_F64)
-    zline_solve_kernel<N, double, double><<<blocks, 128, 0, st>>>(m, (const double *)fac, (const double *)r,
-                                                                  (double *)z, part, done);
+    zline_solve_kernel<N, double, double><<<blocks, 128, zline_smem<N, double>(), st>>>(
+        m, (const double *)fac, (const double *)r, (double *)z, part, done);
   else
-    zline_solve_kernel<N, float, float><<<blocks, 128, 0, st>>>(m, (const float *)fac, (const float *)r,
-                                                                (float *)z, part, done);
+    zline_solve_kernel<N, float, float><<<blocks, 128, zline_smem<N, float>(), st>>>(
+        m, (const float *)fac, (const float *)r, (float *)z, part, done);
   return cudaGetLastError();
 }
 
@@ -389,10 +473,11 @@ size_t tn_zline_block_bytes(const DevMesh &m) {
   return (size_t)m.ncol * m.N * m.N * m.nslab * 2 * M * M * sizeof(double);
 }
 
-size_t tn_zline_factor_bytes(const DevMesh &m) {
-  const size_t M = 3 * m.N;
-  return (size_t)m.ncol * m.N * m.N * m.nslab * 2 * M * M * sizeof(float);
+size_t tn_zline_factor_entries(const DevMesh &m) {
+  return (size_t)m.ncol * m.N * m.N * m.nslab * 2 * zpad(3 * m.N);
 }
+
+size_t tn_zline_factor_bytes(const DevMesh &m) { return tn_zline_factor_entries(m) * sizeof(float); }
 
 int tn_zline_partials(const DevMesh &m) { return (m.ncol * m.N * m.N + 3) / 4; }
 
@@ -420,6 +505,27 @@ cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, const vo
     case 7: return solve_n<7>(m, prec, fac, r, z, part, done, st);
     case 8: return solve_n<8>(m, prec, fac, r, z, part, done, st);
     case 9: return solve_n<9>(m, prec, fac, r, z, part, done, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const int2 *work, int nwork,
+                                 const long long *fac_off, const long long *dof_off, const void *fac,
+                                 const void *r, void *z, double *part, const int *done, cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  const int blocks = (nwork + 3) / 4;
+  switch (N) {
+#define TN_CASE(NN)                                                                                       \
+  case NN:                                                                                               \
+    if (prec == TN_F64)                                                                                  \
+      zline_solve_batch_kernel<NN, double, double><<<blocks, 128, zline_smem<NN, double>(), st>>>(      \
+          meshes, work, nwork, fac_off, dof_off, (const double *)fac, (const double *)r, (double *)z, part, done); \
+    else                                                                                                 \
+      zline_solve_batch_kernel<NN, float, float><<<blocks, 128, zline_smem<NN, float>(), st>>>(          \
+          meshes, work, nwork, fac_off, dof_off, (const float *)fac, (const float *)r, (float *)z, part, done);    \
+    return cudaGetLastError();
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
     default: return cudaErrorInvalidValue;
   }
 }

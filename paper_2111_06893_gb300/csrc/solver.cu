@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr int kRedBlocks = 2 * 152;  // fixed partition of the vector reductions
+constexpr int kRedBlocks = 8 * 152;  // fixed partition of the vector reductions
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -383,21 +383,19 @@ thread_local long long g_launches = 0;
     if (e_ != cudaSuccess) return e_;                 \
   } while (0)
 
-cudaError_t pcg_setup_dinv(const DevMesh &m, size_t n, const double *diag, void *dinv, int prec,
-                           cudaStream_t st) {
+cudaError_t pcg_setup_dinv(size_t n, const double *diag, void *dinv, int prec, cudaStream_t st) {
   g_launches += 1;
   if (prec == TN_F64) k_invert<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (double *)dinv);
   else k_invert<float><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (float *)dinv);
-  (void)m;
   return cudaGetLastError();
 }
 
 // one PCG iteration (five launches), all on stream st
 template <typename T>
-static cudaError_t pcg_iteration(const DevMesh &m, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
+static cudaError_t pcg_iteration(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                  double *part_elem, double *part_red, cudaStream_t st) {
-  TN_CU(tn_launch_apply(m, prec, v.p, v.q, part_elem, nullptr, st));
-  k_alpha<<<1, 256, 0, st>>>(s, part_elem, m.E);
+  TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
+  k_alpha<<<1, 256, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
   k_update<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (T *)v.z, (const T *)v.p,
                                                   (const T *)v.q, (const T *)v.dinv, part_red);
@@ -409,16 +407,16 @@ static cudaError_t pcg_iteration(const DevMesh &m, int prec, size_t n, PcgVector
 }
 
 template <typename T>
-static cudaError_t pcg_iteration_zline(const DevMesh &m, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
+static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                        double *part_elem, double *part_red, cudaStream_t st) {
-  TN_CU(tn_launch_apply(m, prec, v.p, v.q, part_elem, nullptr, st));
-  k_alpha<<<1, 256, 0, st>>>(s, part_elem, m.E);
+  TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
+  k_alpha<<<1, 256, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
   k_update_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (const T *)v.p, (const T *)v.q,
                                                     part_red);
   TN_CU(cudaGetLastError());
-  TN_CU(tn_zline_solve(m, prec, v.zfac, v.r, v.z, v.part_rz, &s->done, st));
-  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, tn_zline_partials(m), part_red, kRedBlocks);
+  TN_CU(sys.zsolve(prec, v.zfac, v.r, v.z, v.part_rz, &s->done, st));
+  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, sys.n_rz_parts, part_red, kRedBlocks);
   TN_CU(cudaGetLastError());
   k_pupdate<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
@@ -427,7 +425,7 @@ static cudaError_t pcg_iteration_zline(const DevMesh &m, int prec, size_t n, Pcg
 // PCG on A x = b in precision T; x holds the initial guess (x0_zero: x = 0).
 // Records `chunk` iterations in a graph and replays it until done.
 template <typename T>
-static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, bool x0_zero, double rtol,
+static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, bool x0_zero, double rtol,
                            int max_iters, int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host,
                            double *part_elem, double *part_red, cudaStream_t st, int *applies,
                            ChunkHook hook = ChunkHook()) {
@@ -437,17 +435,17 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     k_fill<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.x, T(0));
     TN_CU(cudaGetLastError());
   } else {
-    TN_CU(tn_launch_apply(m, prec, v.x, v.q, nullptr, nullptr, st));
+    TN_CU(sys.apply(prec, v.x, v.q, nullptr, st));
     *applies += 1;
   }
   const T *Ax = x0_zero ? nullptr : (const T *)v.q;
   if (zl) {
     k_init_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, part_red);
     TN_CU(cudaGetLastError());
-    TN_CU(tn_zline_solve(m, prec, v.zfac, v.r, v.z, v.part_rz, nullptr, st));
+    TN_CU(sys.zsolve(prec, v.zfac, v.r, v.z, v.part_rz, nullptr, st));
     k_copy<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.p, (const T *)v.z);
     TN_CU(cudaGetLastError());
-    k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, tn_zline_partials(m), part_red, kRedBlocks,
+    k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, sys.n_rz_parts, part_red, kRedBlocks,
                                             rtol * rtol, max_iters);
   } else {
     k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, (T *)v.z, (T *)v.p,
@@ -469,14 +467,18 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     int chunk, prec, E;
     const void *geo;
     DevMesh dm;  // baked into the captured kernel parameters
+    OpSys sys;
     bool operator==(const Key &o) const { return std::memcmp(this, &o, sizeof(Key)) == 0; }
   };
   Key key;
   std::memset(static_cast<void *>(&key), 0, sizeof(key));
   key.x = v.x; key.r = v.r; key.z = v.z; key.p = v.p; key.q = v.q; key.b = v.b; key.dinv = v.dinv;
   key.zfac = v.zfac; key.part_rz = v.part_rz; key.pe = part_elem; key.pr = part_red; key.s = s_dev;
-  key.n = n; key.chunk = chunk; key.prec = prec; key.E = m.E; key.geo = m.colgeo;
-  std::memcpy(&key.dm, &m, sizeof(DevMesh));
+  key.n = n; key.chunk = chunk; key.prec = prec; key.E = sys.n_apply_parts;
+  key.geo = sys.m ? (const void *)sys.m->colgeo : (const void *)sys.meshes;
+  if (sys.m) std::memcpy(static_cast<void *>(&key.dm), sys.m, sizeof(DevMesh));
+  std::memcpy(static_cast<void *>(&key.sys), &sys, sizeof(OpSys));
+  key.sys.m = nullptr;
   static thread_local Key cached_key[2];
   static thread_local cudaGraphExec_t cached_exec[2] = {nullptr, nullptr};
   const int slot = prec == TN_F64 ? 0 : 1;
@@ -490,8 +492,8 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
     TN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t cap = cudaSuccess;
     for (int it = 0; it < chunk && cap == cudaSuccess; ++it)
-      cap = zl ? pcg_iteration_zline<T>(m, prec, n, v, s_dev, part_elem, part_red, st)
-               : pcg_iteration<T>(m, prec, n, v, s_dev, part_elem, part_red, st);
+      cap = zl ? pcg_iteration_zline<T>(sys, prec, n, v, s_dev, part_elem, part_red, st)
+               : pcg_iteration<T>(sys, prec, n, v, s_dev, part_elem, part_red, st);
     cudaError_t endc = cudaStreamEndCapture(st, &graph);
     if (cap != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cap; }
     TN_CU(endc);
@@ -521,25 +523,25 @@ static cudaError_t pcg_run(const DevMesh &m, int prec, size_t n, PcgVectors &v, 
   return err;
 }
 
-cudaError_t pcg_f64(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+cudaError_t pcg_f64(const OpSys &sys, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
                     double *part_red, cudaStream_t st, int *applies, ChunkHook hook) {
-  return pcg_run<double>(m, TN_F64, n, v, x0_zero, rtol, max_iters, chunk, s_dev, s_host, part_elem,
+  return pcg_run<double>(sys, TN_F64, n, v, x0_zero, rtol, max_iters, chunk, s_dev, s_host, part_elem,
                          part_red, st, applies, hook);
 }
 
-cudaError_t pcg_f32(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+cudaError_t pcg_f32(const OpSys &sys, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
                     double *part_red, cudaStream_t st, int *applies) {
-  return pcg_run<float>(m, TN_F32, n, v, x0_zero, rtol, max_iters, chunk, s_dev, s_host, part_elem,
+  return pcg_run<float>(sys, TN_F32, n, v, x0_zero, rtol, max_iters, chunk, s_dev, s_host, part_elem,
                         part_red, st, applies);
 }
 
 // r = b - A x in FP64; returns ||r||^2 in *rr_host (synchronises)
-cudaError_t residual_f64(const DevMesh &m, size_t n, const double *b, const double *x, double *Ax, double *r,
+cudaError_t residual_f64(const OpSys &sys, size_t n, const double *b, const double *x, double *Ax, double *r,
                          double *part_red, double *sum_dev, double *rr_host, cudaStream_t st) {
   g_launches += 3;
-  TN_CU(tn_launch_apply(m, TN_F64, x, Ax, nullptr, nullptr, st));
+  TN_CU(sys.apply(TN_F64, x, Ax, nullptr, st));
   k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(n, b, Ax, r, part_red);
   TN_CU(cudaGetLastError());
   k_finish_sum<<<1, 256, 0, st>>>(part_red, kRedBlocks, sum_dev);
@@ -584,6 +586,31 @@ cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st) {
 }
 
 int reduction_blocks() { return kRedBlocks; }
+
+}  // namespace tn
+
+cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const {
+  if (m) return tn_launch_apply(*m, prec, u, y, part, nullptr, st);
+  for (int g = 0; g < ngroups; ++g) {
+    cudaError_t e = tn_launch_apply_batch(gN[g], prec, meshes, gwork[g], gcount[g], dof_off, u, y,
+                                          part ? part + gpart_off[g] : nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t OpSys::zsolve(int prec, const void *fac, const void *r, void *z, double *part, const int *done,
+                          cudaStream_t st) const {
+  if (m) return tn_zline_solve(*m, prec, fac, r, z, part, done, st);
+  for (int g = 0; g < ngroups; ++g) {
+    cudaError_t e = tn_zline_solve_batch(gN[g], prec, meshes, gline[g], glines[g], fac_off, dof_off, fac, r, z,
+                                         part ? part + grz_off[g] : nullptr, done, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+namespace tn {
 
 // dots a . B_j (j < nb <= 16) summed in a fixed order on the host
 cudaError_t multidot(size_t n, const double *a, const double *const *B_dev, int nb, double *part, double *host_tmp,

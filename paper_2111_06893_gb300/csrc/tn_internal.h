@@ -117,6 +117,12 @@ cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const dou
 // part[b] = partial sums of lam . db/dr0 (beam width derivative of the load)
 cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const double *lam, double *part,
                               int nparts, cudaStream_t st);
+// batches: one launch per polynomial degree; work[b] = (instance, element)
+cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
+                                  const long long *dof_off, const void *u, void *y, double *partial,
+                                  cudaStream_t st);
+cudaError_t tn_launch_energy_batch(int N, const DevMesh *meshes, const int2 *work, int nwork,
+                                   const long long *dof_off, const double *u, double *out, cudaStream_t st);
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
                             double *partial, const void *dotwith, cudaStream_t st);
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st);

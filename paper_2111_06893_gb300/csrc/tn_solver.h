@@ -12,6 +12,27 @@ struct tn_pcg_scalars {
   int iters, max_iters, done, breakdown;
 };
 
+// the operator and preconditioner of a solve: one mesh, or a batch of meshes
+// grouped by polynomial degree (one launch per group)
+struct OpSys {
+  const DevMesh *m = nullptr;  // single mesh (host copy of the struct)
+  const DevMesh *meshes = nullptr;  // batch: device array of the instances' meshes
+  int ngroups = 0;
+  int gN[8] = {0};
+  const int2 *gwork[8] = {nullptr};  // (instance, element) per CTA of the apply
+  int gcount[8] = {0};
+  int gpart_off[8] = {0};
+  const int2 *gline[8] = {nullptr};  // (instance, line) per warp of the z-line solve
+  int glines[8] = {0};
+  int grz_off[8] = {0};
+  const long long *dof_off = nullptr, *fac_off = nullptr;
+  int n_apply_parts = 0;  // partial sums written by one apply
+  int n_rz_parts = 0;     // partial sums written by one z-line solve
+  cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const;
+  cudaError_t zsolve(int prec, const void *fac, const void *r, void *z, double *part, const int *done,
+                     cudaStream_t st) const;
+};
+
 // vectors of one PCG run, all of the run's precision
 struct PcgVectors {
   void *x, *r, *z, *p, *q;
@@ -31,15 +52,14 @@ struct ChunkHook {
 namespace tn {
 // kernel launches issued on behalf of the current solve (host counter)
 extern thread_local long long g_launches;
-cudaError_t pcg_setup_dinv(const DevMesh &m, size_t n, const double *diag, void *dinv, int prec,
-                           cudaStream_t st);
-cudaError_t pcg_f64(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+cudaError_t pcg_setup_dinv(size_t n, const double *diag, void *dinv, int prec, cudaStream_t st);
+cudaError_t pcg_f64(const OpSys &sys, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
                     double *part_red, cudaStream_t st, int *applies, ChunkHook hook = ChunkHook());
-cudaError_t pcg_f32(const DevMesh &m, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
+cudaError_t pcg_f32(const OpSys &sys, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,
                     double *part_red, cudaStream_t st, int *applies);
-cudaError_t residual_f64(const DevMesh &m, size_t n, const double *b, const double *x, double *Ax, double *r,
+cudaError_t residual_f64(const OpSys &sys, size_t n, const double *b, const double *x, double *Ax, double *r,
                          double *part_red, double *sum_dev, double *rr_host, cudaStream_t st);
 cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_dev, double *out_host,
                       cudaStream_t st);

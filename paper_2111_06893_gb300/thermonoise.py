@@ -28,7 +28,8 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 # every entry point declared in include/thermonoise.h
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
-           "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad"]
+           "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
+           "tn_batch_offsets"]
 
 
 class MeshDesc(C.Structure):
@@ -98,6 +99,10 @@ def load():
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
                                      C.POINTER(SolveReport)]),
+        "tn_batch_create": (C.c_int, [vp, C.c_int]),
+        "tn_batch_set": (C.c_int, [vp, C.c_int, C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
+                                   C.c_double, C.c_double]),
+        "tn_batch_offsets": (C.c_int, [vp, i64p, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +201,26 @@ class Context:
 
     def set_beam(self, r0, F0):
         _check(load().tn_set_beam(self._h, float(r0), float(F0)))
+        return self
+
+    def build_batch(self, descs):
+        """Hold many mirrors at once (see tn_batch_create); returns self."""
+        lib = load()
+        _check(lib.tn_batch_create(self._h, len(descs)))
+        for i, d in enumerate(descs):
+            md, keep = mesh_struct(d)
+            mats = material_array(d["materials"])
+            _check(lib.tn_batch_set(self._h, i, C.byref(md), len(d["materials"]), mats,
+                                    float(d["beam"]["r0"]), float(d["beam"]["F0"])))
+            del keep
+        n = len(descs)
+        doff = (C.c_int64 * (n + 1))()
+        loff = (C.c_int * (n + 1))()
+        _check(lib.tn_batch_offsets(self._h, doff, loff))
+        self.descs = list(descs)
+        self.dof_off = np.array(doff[:], dtype=np.int64)
+        self.layer_off = np.array(loff[:], dtype=np.int64)
+        self.desc = {"materials": [None] * int(self.layer_off[-1])}
         return self
 
     @property
@@ -367,7 +392,8 @@ def _energy_fn_class():
         @staticmethod
         def backward(ctx, gU):
             kw = {k: v for k, v in ctx.kw.items() if k in ("mode", "rtol", "inner_rtol", "precond",
-                                                         "max_iter", "max_outer", "check_every")}
+                                                         "max_iter", "max_outer", "check_every",
+                                                         "raise_on_error")}
             g = ctx.tc.energy_grad(ctx.u, gU.detach().cpu().numpy(), **kw)
             return (torch.tensor(g["slab_z"], dtype=torch.float64), torch.tensor(g["r0"], dtype=torch.float64),
                     torch.tensor(g["moduli"], dtype=torch.float64), None, None)

@@ -1,0 +1,58 @@
+"""A batch of mirrors of uneven degree and element count: every mirror's block
+of the batched operator / preconditioner equals the single-mirror result
+bitwise, and the batched solve gives each mirror's energies (oracle parity)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Mesh, Operator, observables as ob
+
+from cases import box_layers, box_tiny, cyl_small
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_06893_gb300 import build
+    build.build()
+
+
+def batch_descs():
+    return [box_tiny(2), cyl_small(3, 1), box_layers(4), cyl_small(4, 1, thick=(0.03,)),
+            W.sweep_instance(3), box_tiny(5)]
+
+
+def test_batch_blocks_equal_single_mirror_results():
+    from paper_2111_06893_gb300 import thermonoise
+    descs = batch_descs()
+    bc = thermonoise.Context().build_batch(descs)
+    off = bc.dof_off
+    rng = np.random.default_rng(0)
+    for dtype in (torch.float64, torch.float32):
+        u = torch.tensor(rng.uniform(-1, 1, size=int(off[-1])), dtype=dtype, device="cuda")
+        y = bc.apply_operator(u)
+        z = bc.precond_apply(u, precond="zline")
+        for i, d in enumerate(descs):
+            sc = thermonoise.setup(d)
+            ui = u[off[i]:off[i + 1]].clone()
+            assert torch.equal(y[off[i]:off[i + 1]], sc.apply_operator(ui)), (i, dtype)
+            assert torch.equal(z[off[i]:off[i + 1]], sc.precond_apply(ui, precond="zline")), (i, dtype)
+
+
+def test_batched_solve_energies_match_oracle():
+    from paper_2111_06893_gb300 import thermonoise
+    descs = batch_descs()[:4]
+    bc = thermonoise.Context().build_batch(descs)
+    for mode in ("f64", "mixed"):
+        u, rep = bc.solve(mode=mode, rtol=1e-12, energy_rtol=1e-12)
+        U = bc.layer_energies(u)
+        for i, d in enumerate(descs):
+            op = Operator(Mesh(d))
+            A = op.assemble()
+            Uo = ob.layer_energies(op, ob.solve_dense(A, op.rhs()))
+            Ui = U[bc.layer_off[i]:bc.layer_off[i + 1]]
+            assert np.max(np.abs(Ui - Uo) / Uo) < 1e-9, (mode, i, Ui, Uo, rep)
