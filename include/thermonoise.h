@@ -238,11 +238,19 @@ tn_status tn_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const double *u
  *     once (one Krylov iteration serves every mirror; the energy test covers
  *     every layer of every mirror);
  *   - tn_layer_energies returns the energies of all layers of all mirrors.
- * tn_diagonal, TN_PC_JACOBI and tn_energy_grad need a single mesh. */
+ * tn_diagonal and TN_PC_JACOBI need a single mesh; gradients of a batch
+ * come from tn_batch_energy_grad. */
 tn_status tn_batch_create(tn_ctx *ctx, int n_instances);
 tn_status tn_batch_set(tn_ctx *ctx, int instance, const tn_mesh_desc *desc, int n_materials,
                        const tn_material *m, double r0, double F0);
 tn_status tn_batch_offsets(const tn_ctx *ctx, int64_t *dof_off, int *layer_off);
+/* tn_energy_grad for every mirror of a batch at once: one batched adjoint
+ * solve, then the per-mirror contractions.  w_host: weights of all layers
+ * (concatenated like the energies); outputs concatenated mirror by mirror:
+ * dJ_dslab_z[sum_i (n_slabs_i + 1)], dJ_dr0[n], dJ_dmat[3 * all layers]. */
+tn_status tn_batch_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const double *u_dev, const double *w_host,
+                               double *lambda_dev, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                               tn_solve_report *rep);
 
 /* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
  * per layer, dissipated power 2 pi f sum_i phi_i U_i):

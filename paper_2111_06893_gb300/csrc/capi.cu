@@ -54,6 +54,8 @@ struct BatchInst {
   long long dof_off = 0, fac_off = 0;
   int layer_off = 0;
   bool set = false;
+  std::vector<double> slab_z;
+  std::vector<int> slab_log;
 };
 
 struct Batch {
@@ -726,6 +728,8 @@ tn_status tn_batch_set(tn_ctx *c, int i, const tn_mesh_desc *d, int n_mat, const
   m.layer_c = q.layer_c; m.colgeo32 = q.colgeo32; m.slabgeo32 = q.slabgeo32; m.layer_c32 = q.layer_c32;
   q.r0 = r0;
   q.F0 = F0;
+  q.slab_z.assign(d->slab_z, d->slab_z + hm.nslab + 1);
+  q.slab_log.assign(d->slab_log, d->slab_log + hm.nslab);
   q.set = true;
   for (int k = 0; k < b->n; ++k)
     if (!b->inst[k].set) return TN_OK;
@@ -1016,65 +1020,23 @@ static double host_sum(const double *dev, int n, double *tmp, cudaStream_t st, c
   return s;
 }
 
-tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, const double *w_host,
-                         double *lambda, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
-                         tn_solve_report *rep) {
-  tn_status st = need_ready(c, true);
-  if (st) return st;
-  if (!o || !w_host || !dJ_dslab_z || !dJ_dr0 || !dJ_dmat) return fail(TN_EINVAL, "null argument");
-  if (is_batch(c)) return fail(TN_EINVAL, "tn_energy_grad works on a single mesh");
-  if ((st = check_buf(c, u, 8, "u"))) return st;
-  if (lambda && (st = check_buf(c, lambda, 8, "lambda"))) return st;
-  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
-  if ((st = ensure_ws(c))) return st;
-  const tn::HostMesh &hm = c->hm;
+// dJ/dtheta for every parameter of one mirror, given u, lambda and the layer
+// weights on the device: dual-number operator / energy contractions launched
+// over the slabs a parameter touches; partial sums reduced on the host in a
+// fixed order.  part: device scratch of >= E + 1024 doubles, tmp: host scratch
+// of the same size.
+static cudaError_t grad_contractions(const tn::HostMesh &hm, const DevMesh &dm, const double *slab_z,
+                                     const int *slab_log, const double *u, const double *lam, const double *wdev,
+                                     double r0, double F0, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                                     double *part, double *tmp, double *seed_dev, double *matseed, cudaStream_t s) {
   const int S = hm.nslab, nl = hm.n_layers, N = hm.N;
-  const size_t n = c->ndof, E = (size_t)hm.E;
-  double *wdev = nullptr, *g = nullptr, *lam = lambda, *part = nullptr, *seed_dev = nullptr, *matseed = nullptr;
-  double *tmp = (double *)std::malloc(sizeof(double) * (E + 1024));
-  double *seed = (double *)std::malloc(sizeof(double) * (size_t)S * N);
-  double *sz = (double *)std::malloc(sizeof(double) * (S + 1));
-  int *slog = (int *)std::malloc(sizeof(int) * S);
-  cudaError_t e = (tmp && seed && sz && slog) ? cudaSuccess : cudaErrorMemoryAllocation;
-  if (e == cudaSuccess) e = cudaMalloc((void **)&wdev, sizeof(double) * nl);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&g, sizeof(double) * n);
-  if (e == cudaSuccess && !lam) e = cudaMalloc((void **)&lam, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * (E + 1024));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * (size_t)S * N);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 3 * nl);
-  tn_solve_report r{};
-  cudaStream_t s = c->stream;
-  auto cleanup = [&]() {
-    if (wdev) cudaFree(wdev);
-    if (g) cudaFree(g);
-    if (lam && lam != lambda) cudaFree(lam);
-    if (part) cudaFree(part);
-    if (seed_dev) cudaFree(seed_dev);
-    if (matseed) cudaFree(matseed);
-    std::free(tmp); std::free(seed); std::free(sz); std::free(slog);
-  };
-  if (e != cudaSuccess) { cleanup(); cudaGetLastError(); return fail(TN_ENOMEM, "gradient workspace"); }
-  // slab positions and maps, recovered from the host mesh tables
-  sz[0] = 0.0;
-  for (int q = 0; q < S; ++q) {
-    slog[q] = c->slab_log_host[q];
-    sz[q + 1] = c->slab_z_host[q + 1];
-  }
-  // adjoint: A lambda = g = sum_i w_i K_i u  (A is symmetric)
-  e = cudaMemcpyAsync(wdev, w_host, sizeof(double) * nl, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = tn_launch_energy_source(c->dm, u, wdev, g, s);
-  if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "adjoint source"); }
-  tn_solve_opts ao = *o;
-  ao.energy_rtol = 0.0;
-  st = solve_impl(c, &ao, g, lam, &r);
-  if (st != TN_OK && st != TN_ENOTCONV) { cleanup(); return st; }
-  tn_status result = st;
-  // slab boundary positions
+  std::vector<double> seed((size_t)S * N);
+  cudaError_t e = cudaSuccess;
   dJ_dslab_z[0] = 0.0;
   for (int b = 1; b <= S && e == cudaSuccess; ++b) {
-    slab_seed(hm, sz, slog, b, seed);
-    e = cudaMemcpyAsync(seed_dev, seed, sizeof(double) * (size_t)S * N, cudaMemcpyHostToDevice, s);
-    DevMesh m = c->dm;
+    slab_seed(hm, slab_z, slab_log, b, seed.data());
+    e = cudaMemcpyAsync(seed_dev, seed.data(), sizeof(double) * (size_t)S * N, cudaMemcpyHostToDevice, s);
+    DevMesh m = dm;
     m.d_slabdz = seed_dev;
     const int a0 = b - 2 < 0 ? 0 : b - 2, a1 = b + 2 > S ? S : b + 2;
     const int k0 = b - 1 < 0 ? 0 : b - 1, k1 = b + 1 > S ? S : b + 1;
@@ -1084,7 +1046,6 @@ tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, con
     const double dK = e == cudaSuccess ? host_sum(part, (k1 - k0) * hm.ncol, tmp, s, &e) : 0.0;
     dJ_dslab_z[b] = dK - dAu;
   }
-  // moduli c11, c12, c44 of every layer
   for (int L = 0; L < nl && e == cudaSuccess; ++L) {
     int lo = S, hi = -1;
     for (int q = 0; q < S; ++q)
@@ -1095,7 +1056,7 @@ tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, con
       for (int t = 0; t < 3 * nl; ++t) tmp[t] = (t == 3 * L + q) ? 1.0 : 0.0;
       e = cudaMemcpyAsync(matseed, tmp, sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      DevMesh m = c->dm;
+      DevMesh m = dm;
       m.d_layer_c = matseed;
       const int a0 = lo - 1 < 0 ? 0 : lo - 1, a1 = hi + 2 > S ? S : hi + 2;
       if (e == cudaSuccess) e = tn_launch_apply_dual(m, a0, a1, u, lam, part, s);
@@ -1105,13 +1066,102 @@ tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, con
       dJ_dmat[3 * L + q] = dK - dAu;
     }
   }
-  // beam width: only the load depends on r0
-  if (e == cudaSuccess) e = tn_launch_rhs_dr0(c->dm, c->r0, c->F0, lam, part, 256, s);
+  if (e == cudaSuccess) e = tn_launch_rhs_dr0(dm, r0, F0, lam, part, 256, s);
   if (e == cudaSuccess) *dJ_dr0 = host_sum(part, 256, tmp, s, &e);
+  return e;
+}
+
+// the adjoint gradient of the context's mirror or batch (see the header)
+static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, const double *w_host,
+                           double *lambda, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                           tn_solve_report *rep) {
+  tn_status st = need_ready(c, true);
+  if (st) return st;
+  if (!o || !w_host || !dJ_dslab_z || !dJ_dr0 || !dJ_dmat) return fail(TN_EINVAL, "null argument");
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (lambda && (st = check_buf(c, lambda, 8, "lambda"))) return st;
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  const int nl = total_layers(c);
+  const size_t n = c->ndof;
+  size_t Emax = 0, SNmax = 0;
+  int NLmax = 0;
+  if (is_batch(c)) {
+    for (int i = 0; i < c->batch->n; ++i) {
+      const tn::HostMesh &hm = c->batch->inst[i].hm;
+      Emax = (size_t)hm.E > Emax ? (size_t)hm.E : Emax;
+      SNmax = (size_t)hm.nslab * hm.N > SNmax ? (size_t)hm.nslab * hm.N : SNmax;
+      NLmax = hm.n_layers > NLmax ? hm.n_layers : NLmax;
+    }
+  } else {
+    Emax = c->hm.E; SNmax = (size_t)c->hm.nslab * c->hm.N; NLmax = c->hm.n_layers;
+  }
+  double *wdev = nullptr, *g = nullptr, *lam = lambda, *part = nullptr, *seed_dev = nullptr, *matseed = nullptr;
+  std::vector<double> tmp(Emax + 1024 + 3 * (size_t)NLmax);
+  cudaError_t e = cudaMalloc((void **)&wdev, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&g, sizeof(double) * n);
+  if (e == cudaSuccess && !lam) e = cudaMalloc((void **)&lam, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * (Emax + 1024));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * SNmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 3 * NLmax);
+  tn_solve_report r{};
+  cudaStream_t s = c->stream;
+  auto cleanup = [&]() {
+    if (wdev) cudaFree(wdev);
+    if (g) cudaFree(g);
+    if (lam && lam != lambda) cudaFree(lam);
+    if (part) cudaFree(part);
+    if (seed_dev) cudaFree(seed_dev);
+    if (matseed) cudaFree(matseed);
+  };
+  if (e != cudaSuccess) { cleanup(); cudaGetLastError(); return fail(TN_ENOMEM, "gradient workspace"); }
+  // adjoint source g = sum_i w_i K_i u per mirror
+  e = cudaMemcpyAsync(wdev, w_host, sizeof(double) * nl, cudaMemcpyHostToDevice, s);
+  if (!is_batch(c)) {
+    if (e == cudaSuccess) e = tn_launch_energy_source(c->dm, u, wdev, g, s);
+  } else {
+    for (int i = 0; i < c->batch->n && e == cudaSuccess; ++i) {
+      const BatchInst &q = c->batch->inst[i];
+      e = tn_launch_energy_source(q.dm, u + q.dof_off, wdev + q.layer_off, g + q.dof_off, s);
+    }
+  }
+  if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "adjoint source"); }
+  tn_solve_opts ao = *o;
+  ao.energy_rtol = 0.0;
+  st = solve_impl(c, &ao, g, lam, &r);
+  if (st != TN_OK && st != TN_ENOTCONV) { cleanup(); return st; }
+  tn_status result = st;
+  if (!is_batch(c)) {
+    e = grad_contractions(c->hm, c->dm, c->slab_z_host, c->slab_log_host, u, lam, wdev, c->r0, c->F0, dJ_dslab_z,
+                          dJ_dr0, dJ_dmat, part, tmp.data(), seed_dev, matseed, s);
+  } else {
+    size_t zoff = 0;
+    for (int i = 0; i < c->batch->n && e == cudaSuccess; ++i) {
+      const BatchInst &q = c->batch->inst[i];
+      e = grad_contractions(q.hm, q.dm, q.slab_z.data(), q.slab_log.data(), u + q.dof_off, lam + q.dof_off,
+                            wdev + q.layer_off, q.r0, q.F0, dJ_dslab_z + zoff, dJ_dr0 + i,
+                            dJ_dmat + 3 * (size_t)q.layer_off, part, tmp.data(), seed_dev, matseed, s);
+      zoff += q.hm.nslab + 1;
+    }
+  }
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "gradient contractions");
   if (rep) *rep = r;
   return result;
+}
+
+tn_status tn_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, const double *w_host,
+                         double *lambda, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                         tn_solve_report *rep) {
+  if (c && is_batch(c)) return fail(TN_EINVAL, "tn_energy_grad works on a single mesh; use tn_batch_energy_grad");
+  return grad_impl(c, o, u, w_host, lambda, dJ_dslab_z, dJ_dr0, dJ_dmat, rep);
+}
+
+tn_status tn_batch_energy_grad(tn_ctx *c, const tn_solve_opts *o, const double *u, const double *w_host,
+                               double *lambda, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
+                               tn_solve_report *rep) {
+  if (c && !is_batch(c)) return fail(TN_EINVAL, "tn_batch_energy_grad needs a batch");
+  return grad_impl(c, o, u, w_host, lambda, dJ_dslab_z, dJ_dr0, dJ_dmat, rep);
 }
 
 tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {

@@ -853,8 +853,15 @@ __device__ __forceinline__ void apply2_body(const DevMesh &m, const int e, const
   }
 }
 
+// resident CTAs per SM requested from the register allocator for the
+// line-task kernel (FP32, N <= 7: four CTAs of nthreads<N>() threads)
 template <int N, typename T>
-__global__ void __launch_bounds__(nthreads<N>())
+__host__ __device__ constexpr int apply2_min_blocks() {
+  return 1;  // measured: forcing 4 CTAs/SM at N = 7 spills and runs slower
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(nthreads<N>(), apply2_min_blocks<N, T>())
 apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   apply2_body<N, T>(m, e0 + blockIdx.x, u, y, partial ? partial + blockIdx.x : nullptr, smem_raw);
@@ -862,7 +869,7 @@ apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ 
 
 // a batch of meshes: CTA b works on element work[b].y of instance work[b].x
 template <int N, typename T>
-__global__ void __launch_bounds__(nthreads<N>())
+__global__ void __launch_bounds__(nthreads<N>(), apply2_min_blocks<N, T>())
 apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work,
                     const long long *__restrict__ dof_off, const T *__restrict__ u, T *__restrict__ y,
                     double *__restrict__ partial) {

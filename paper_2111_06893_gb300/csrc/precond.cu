@@ -452,11 +452,22 @@ cudaError_t setup_n(const DevMesh &m, double *blk, float *fac, double *fac64, in
   return cudaGetLastError();
 }
 
+// opt in to more than 48 KB of dynamic shared memory (FP64, large N)
+template <typename K>
+cudaError_t zline_smem_optin(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <int N>
 cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, const void *r, void *z, double *part,
                     const int *done, cudaStream_t st) {
   const int nlines = m.ncol * N * N;
   const int blocks = (nlines + 3) / 4;
+  cudaError_t err = prec == TN_F64
+                        ? zline_smem_optin(zline_solve_kernel<N, double, double>, zline_smem<N, double>())
+                        : zline_smem_optin(zline_solve_kernel<N, float, float>, zline_smem<N, float>());
+  if (err != cudaSuccess) return err;
   if (prec == TN_F64)
     zline_solve_kernel<N, double, double><<<blocks, 128, zline_smem<N, double>(), st>>>(
         m, (const double *)fac, (const double *)r, (double *)z, part, done);
@@ -517,6 +528,12 @@ cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const i
   switch (N) {
 #define TN_CASE(NN)                                                                                       \
   case NN:                                                                                               \
+    {                                                                                                    \
+      cudaError_t oe = prec == TN_F64                                                                    \
+          ? zline_smem_optin(zline_solve_batch_kernel<NN, double, double>, zline_smem<NN, double>())     \
+          : zline_smem_optin(zline_solve_batch_kernel<NN, float, float>, zline_smem<NN, float>());       \
+      if (oe != cudaSuccess) return oe;                                                                  \
+    }                                                                                                    \
     if (prec == TN_F64)                                                                                  \
       zline_solve_batch_kernel<NN, double, double><<<blocks, 128, zline_smem<NN, double>(), st>>>(      \
           meshes, work, nwork, fac_off, dof_off, (const double *)fac, (const double *)r, (double *)z, part, done); \

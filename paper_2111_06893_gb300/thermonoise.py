@@ -29,7 +29,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
-           "tn_batch_offsets"]
+           "tn_batch_offsets", "tn_batch_energy_grad"]
 
 
 class MeshDesc(C.Structure):
@@ -103,6 +103,8 @@ def load():
         "tn_batch_set": (C.c_int, [vp, C.c_int, C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
                                    C.c_double, C.c_double]),
         "tn_batch_offsets": (C.c_int, [vp, i64p, C.POINTER(C.c_int)]),
+        "tn_batch_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
+                                           C.POINTER(SolveReport)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +220,7 @@ class Context:
         loff = (C.c_int * (n + 1))()
         _check(lib.tn_batch_offsets(self._h, doff, loff))
         self.descs = list(descs)
+        self.desc = None
         self.dof_off = np.array(doff[:], dtype=np.int64)
         self.layer_off = np.array(loff[:], dtype=np.int64)
         self.desc = {"materials": [None] * int(self.layer_off[-1])}
@@ -290,19 +293,29 @@ class Context:
         w = np.ascontiguousarray(w, dtype=np.float64)
         if w.shape != (nl,):
             raise ValueError(f"w needs {nl} values")
-        ns = len(self.desc["slab_z"]) - 1
-        gz = np.zeros(ns + 1)
-        gr = np.zeros(1)
+        batched = getattr(self, "descs", None) is not None
+        descs = self.descs if batched else [self.desc]
+        ns = sum(len(d["slab_z"]) for d in descs)
+        gz = np.zeros(ns)
+        gr = np.zeros(len(descs))
         gm = np.zeros(3 * nl)
         o = self._opts(mode, rtol, inner_rtol, max_iter, max_outer, check_every, precond, 0.0)
         rep = SolveReport()
         dp = C.POINTER(C.c_double)
-        st = load().tn_energy_grad(self._h, C.byref(o), C.c_void_p(u.data_ptr()), w.ctypes.data_as(dp), None,
-                                   gz.ctypes.data_as(dp), gr.ctypes.data_as(dp), gm.ctypes.data_as(dp),
-                                   C.byref(rep))
+        fn = load().tn_batch_energy_grad if batched else load().tn_energy_grad
+        st = fn(self._h, C.byref(o), C.c_void_p(u.data_ptr()), w.ctypes.data_as(dp), None,
+                gz.ctypes.data_as(dp), gr.ctypes.data_as(dp), gm.ctypes.data_as(dp), C.byref(rep))
         if raise_on_error:
             _check(st)
-        return {"slab_z": gz, "r0": float(gr[0]), "moduli": gm.reshape(nl, 3), "report": rep.as_dict()}
+        if not batched:
+            return {"slab_z": gz, "r0": float(gr[0]), "moduli": gm.reshape(nl, 3), "report": rep.as_dict()}
+        out, zo = [], 0
+        for i, d in enumerate(descs):
+            nz = len(d["slab_z"])
+            lo, hi = int(self.layer_off[i]), int(self.layer_off[i + 1])
+            out.append({"slab_z": gz[zo:zo + nz], "r0": float(gr[i]), "moduli": gm.reshape(nl, 3)[lo:hi]})
+            zo += nz
+        return {"instances": out, "report": rep.as_dict()}
 
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",

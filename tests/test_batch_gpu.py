@@ -56,3 +56,23 @@ def test_batched_solve_energies_match_oracle():
             Uo = ob.layer_energies(op, ob.solve_dense(A, op.rhs()))
             Ui = U[bc.layer_off[i]:bc.layer_off[i + 1]]
             assert np.max(np.abs(Ui - Uo) / Uo) < 1e-9, (mode, i, Ui, Uo, rep)
+
+
+def test_batched_gradients_equal_single_mirror_gradients():
+    from paper_2111_06893_gb300 import thermonoise
+    descs = batch_descs()[:3]
+    bc = thermonoise.Context().build_batch(descs)
+    u, _ = bc.solve(mode="f64", rtol=1e-13, energy_rtol=1e-14, raise_on_error=False)
+    nl = int(bc.layer_off[-1])
+    w = np.random.default_rng(2).uniform(0.5, 2.0, size=nl)
+    gb = bc.energy_grad(u, w, mode="f64", rtol=1e-13, raise_on_error=False)
+    for i, d in enumerate(descs):
+        sc = thermonoise.setup(d)
+        ui, _ = sc.solve(mode="f64", rtol=1e-13, energy_rtol=1e-14, raise_on_error=False)
+        wi = w[bc.layer_off[i]:bc.layer_off[i + 1]]
+        gs = sc.energy_grad(ui, wi, mode="f64", rtol=1e-13, raise_on_error=False)
+        gi = gb["instances"][i]
+        scale = np.abs(gs["slab_z"]).max()
+        assert np.max(np.abs(gi["slab_z"] - gs["slab_z"])) <= 1e-7 * scale, (i, gi["slab_z"], gs["slab_z"])
+        assert abs(gi["r0"] - gs["r0"]) <= 1e-7 * abs(gs["r0"])
+        assert np.max(np.abs(gi["moduli"] - gs["moduli"])) <= 1e-7 * np.abs(gs["moduli"]).max()
