@@ -190,7 +190,9 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-13)
     ap.add_argument("--energy-rtol", type=float, default=1e-10,
                     help="stop once every U_i changes by less than this between checks")
-    ap.add_argument("--inner-rtol", type=float, default=0.05)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--inner-max", type=int, default=300)
+    ap.add_argument("--fcg-window", type=int, default=16)
     ap.add_argument("--precond", default="zline", choices=["zline", "jacobi"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-U solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -285,7 +287,8 @@ def main():
 
     def step():
         _, rep = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u,
-                           energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False)
+                           energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False,
+                           inner_max=args.inner_max, fcg_window=args.fcg_window)
         U = ctx.layer_energies(u)
         S = [thermonoise.noise_psd(U[lofs[i]:lofs[i + 1]], phis[i], KB_T, FREQ, d["beam"]["F0"])
              for i, d in enumerate(descs)]
@@ -373,7 +376,8 @@ def main():
             ctx.set_materials(desc["materials"])
             ctx.set_beam(desc["beam"]["r0"], desc["beam"]["F0"])
         _, rep_e = ctx.solve(mode="mixed", rtol=args.rtol, inner_rtol=args.inner_rtol, out=u,
-                             energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False)
+                             energy_rtol=args.energy_rtol, precond=args.precond, raise_on_error=False,
+                             inner_max=args.inner_max, fcg_window=args.fcg_window)
         u_host.copy_(u, non_blocking=True)
         U_e = ctx.layer_energies(u)
         for i, d in enumerate(descs):
@@ -401,6 +405,7 @@ def main():
                    "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
                    "step": "rhs+mixed solve+energies+psd",
                    "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
+                   "inner_max": args.inner_max, "fcg_window": args.fcg_window,
                    "precond": args.precond, "l2": "flushed between steps (256 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_U_s": {"mixed": mixed_s, "fp64": t_fp64,

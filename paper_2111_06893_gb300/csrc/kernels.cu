@@ -857,7 +857,10 @@ __device__ __forceinline__ void apply2_body(const DevMesh &m, const int e, const
 // line-task kernel (FP32, N <= 7: four CTAs of nthreads<N>() threads)
 template <int N, typename T>
 __host__ __device__ constexpr int apply2_min_blocks() {
-  return 1;  // measured: forcing 4 CTAs/SM at N = 7 spills and runs slower
+  // FP32: the CTAs per SM that fit ~60 registers per thread (N = 7: three
+  // CTAs of 352 threads; forcing four spills and runs slower); FP64: one
+  if (sizeof(T) != 4) return 1;
+  return N <= 4 ? 8 : (N == 5 ? 6 : (N == 6 ? 4 : (N == 7 ? 3 : (N == 8 ? 2 : 1))));
 }
 
 template <int N, typename T>

@@ -319,7 +319,7 @@ class Context:
 
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",
-              energy_rtol=0.0, inner_max=30, fcg_window=8):
+              energy_rtol=0.0, inner_max=300, fcg_window=16):
         o = SolveOpts()
         o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
         o.precond = PRECONDS[precond]

@@ -26,8 +26,17 @@ def layered_box():
 
 
 def thin_cylinder():
-    return W.cylinder(10.0, 10.0, [0.02, 0.05], [W.CRYSTAL_B, W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 2,
-                      r0=1.3)
+    d = W.cylinder(10.0, 10.0, [0.02, 0.05], [W.CRYSTAL_B, W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 2,
+                   r0=1.3)
+    # geometric substrate slabs share one depth ratio, so the face sizes h
+    # of the two slabs meeting at the inner substrate boundary are equal and
+    # min(h, h_ext) has a kink there: the energies have only one-sided
+    # derivatives in slab_z[2] and slab_z[3].  Moving that boundary off the
+    # geometric sequence makes every slab derivative two-sided.
+    z = list(d["slab_z"])
+    z[3] = -0.9
+    d["slab_z"] = z
+    return d
 
 
 def iso_chain(m):
@@ -41,8 +50,12 @@ def iso_chain(m):
     return base, dY, dn
 
 
-@pytest.mark.parametrize("make", [layered_box, thin_cylinder])
-def test_adjoint_gradient_matches_oracle_complex_step(make):
+# tolerance: the layered box is well conditioned (both solves accurate to
+# ~1e-13); the thin-coating cylinder (C = 100, 0.02-thick layers) has
+# cond(A) ~ 1e8, so both the oracle's direct solve and the GPU solves carry
+# ~1e-8 relative error into u and lambda
+@pytest.mark.parametrize("make,tol", [(layered_box, 1e-8), (thin_cylinder, 1e-6)])
+def test_adjoint_gradient_matches_oracle_complex_step(make, tol):
     from paper_2111_06893_gb300 import thermonoise
     desc = make()
     ctx = thermonoise.setup(desc)
@@ -59,21 +72,21 @@ def test_adjoint_gradient_matches_oracle_complex_step(make):
     for s in range(1, ns + 1):
         ref = float(np.dot(w, G.energy_derivative(desc, ("slab_z", s))))
         scale = max(abs(ref), 1e-3 * max(abs(v) for v in g["slab_z"]))
-        assert abs(g["slab_z"][s] - ref) <= 1e-8 * scale, ("slab_z", s, g["slab_z"][s], ref)
+        assert abs(g["slab_z"][s] - ref) <= tol * scale, ("slab_z", s, g["slab_z"][s], ref)
     ref = float(np.dot(w, G.energy_derivative(desc, ("r0",))))
-    assert abs(g["r0"] - ref) <= 1e-8 * abs(ref), ("r0", g["r0"], ref)
+    assert abs(g["r0"] - ref) <= tol * abs(ref), ("r0", g["r0"], ref)
     # moduli: cubic layers directly, isotropic through (Y, nu)
     for L, m in enumerate(desc["materials"]):
         if m["kind"] == "cubic":
             for q, key in enumerate(["c11", "c12", "c44"]):
                 ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
-                assert abs(g["moduli"][L, q] - ref) <= 1e-8 * abs(ref), (L, key, g["moduli"][L, q], ref)
+                assert abs(g["moduli"][L, q] - ref) <= tol * abs(ref), (L, key, g["moduli"][L, q], ref)
         else:
             _, dY, dn = iso_chain(m)
             for key, dc in (("Y", dY), ("nu", dn)):
                 ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
                 got = float(np.dot(g["moduli"][L], dc))
-                assert abs(got - ref) <= 1e-6 * abs(ref), (L, key, got, ref)
+                assert abs(got - ref) <= max(tol, 1e-6) * abs(ref), (L, key, got, ref)
 
 
 def test_gradient_matches_gpu_finite_differences_and_autograd():
