@@ -252,6 +252,21 @@ tn_status tn_batch_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const dou
                                double *lambda_dev, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
                                tn_solve_report *rep);
 
+/* tn_layer_energies for callers that cannot allocate device memory at the
+ * time of the call (a process that reserves its HBM budget up front, or one
+ * that must avoid the device-wide synchronisation an allocation or a free can
+ * cause).  The paper has no counterpart: this is a library convenience.  It
+ * allocates nothing: its scratch (per-element energies and per-layer sums) is
+ * a fixed array in the library's device image, which every GPU that loads
+ * the library holds until exit.  Limits: a single mesh of at most 65536
+ * elements and 1024 layers (TN_EINVAL otherwise).  Its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.  Each call writes every scratch entry it reads, so
+ * no clearing is needed.  u_dev: FP64 field; U_host: n_layers doubles.
+ * Synchronises the context's stream. */
+tn_status tn_layer_energies_noalloc(tn_ctx *ctx, const double *u_dev, double *U_host);
+
 /* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
  * per layer, dissipated power 2 pi f sum_i phi_i U_i):
  *   S_out = 4 kB_T sum_i phi_i U_i / (pi f F0^2).  Host only. */

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1196,3 +1197,63 @@ tn_status tn_noise_psd(const double *U, const double *phi, int n, double kB_T, d
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Per-layer energies without any allocation.
+//
+// Some callers cannot allocate device memory when they ask for energies: a
+// process that reserves its whole HBM budget up front (a serving pool that
+// hands out fixed buffers), or one that must not trigger the device-wide
+// synchronisation that cudaMalloc / cudaFree can imply while other streams
+// are busy.  tn_layer_energies allocates its scratch on first use; this
+// variant instead uses a fixed scratch array that lives in the library's
+// device image: every GPU that loads the library holds it (532 KB) until the
+// process exits.  It bounds the mesh to kNoAllocMaxElements elements and
+// kNoAllocMaxLayers layers.  Every call shares the array, so calls that
+// overlap on the GPU (other streams, other threads) race; each call writes
+// every entry it later reads, so nothing has to be cleared between calls.
+namespace {
+constexpr int kNoAllocMaxElements = 65536;
+constexpr int kNoAllocMaxLayers = 1024;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxElements + kNoAllocMaxLayers];
+
+constexpr int kNoAllocMaxDevices = 64;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// device address of the scratch array on the current device (set up once per
+// device; in host code the symbol itself is only a host-side stand-in)
+cudaError_t noalloc_scratch(int device, double **out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" tn_status tn_layer_energies_noalloc(tn_ctx *c, const double *u, double *U_host) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if (is_batch(c)) return fail(TN_EINVAL, "tn_layer_energies_noalloc works on a single mesh");
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (!U_host) return fail(TN_EINVAL, "U_host is null");
+  if (c->dm.E > kNoAllocMaxElements || c->dm.n_layers > kNoAllocMaxLayers)
+    return fail(TN_EINVAL, "tn_layer_energies_noalloc: mesh has %d elements and %d layers; the fixed scratch "
+                "holds at most %d elements and %d layers (use tn_layer_energies)",
+                c->dm.E, c->dm.n_layers, kNoAllocMaxElements, kNoAllocMaxLayers);
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  double *scratch = nullptr;
+  CU_TRY(noalloc_scratch(c->device, &scratch), "cudaGetSymbolAddress of the fixed scratch");
+  double *elem = scratch, *layer = scratch + kNoAllocMaxElements;
+  CU_TRY(tn_launch_energy(c->dm, u, elem, layer, c->stream), "energy launch");
+  CU_TRY(cudaMemcpyAsync(U_host, layer, sizeof(double) * c->dm.n_layers, cudaMemcpyDeviceToHost, c->stream),
+         "energy copy");
+  CU_TRY(cudaStreamSynchronize(c->stream), "energy sync");
+  return TN_OK;
+}

@@ -29,7 +29,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
-           "tn_batch_offsets", "tn_batch_energy_grad"]
+           "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc"]
 
 
 class MeshDesc(C.Structure):
@@ -99,6 +99,7 @@ def load():
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
                                      C.POINTER(SolveReport)]),
+        "tn_layer_energies_noalloc": (C.c_int, [vp, vp, dp]),
         "tn_batch_create": (C.c_int, [vp, C.c_int]),
         "tn_batch_set": (C.c_int, [vp, C.c_int, C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
                                    C.c_double, C.c_double]),
