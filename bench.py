@@ -254,9 +254,23 @@ def main():
             e1.record(stream)
             e1.synchronize()
             res[name] = e0.elapsed_time(e1) / reps_n * 1e3
+        # the column-line preconditioner solve (one launch per application)
+        zres = {}
+        for name, x, y, reps_n in (("f32", x32, y32, 20), ("f64", x64, y64, 10)):
+            for _ in range(3):
+                ctx.precond_apply(x, y, precond="zline")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps_n):
+                ctx.precond_apply(x, y, precond="zline")
+            e1.record(stream)
+            e1.synchronize()
+            zres[name] = e0.elapsed_time(e1) / reps_n * 1e3
         if rank == 0:
             print(json.dumps({"mode": "apply", "workload": args.workload, "ndof": ndof, "us": res,
-                              "gdofs": {k: ndof / v / 1e3 for k, v in res.items()}}), flush=True)
+                              "gdofs": {k: ndof / v / 1e3 for k, v in res.items()},
+                              "zline_us": zres}), flush=True)
         return
 
     # FP64 reference energies: GPU FP64 solve run to its rounding floor

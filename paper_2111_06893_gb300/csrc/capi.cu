@@ -241,8 +241,8 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   cudaError_t e = cudaMalloc((void **)&blk, bb);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac, fb);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->zfac64, 2 * fb);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zpart, sizeof(double) * nparts);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zstatus, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zpart, sizeof(double) * 2 * nparts);  // r.z, r.r
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->zstatus, 2 * sizeof(int));  // factor status, solve timeout
   if (e != cudaSuccess) {
     if (blk) cudaFree(blk);
     free_precond(c);
@@ -250,7 +250,7 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
     return fail(TN_ENOMEM, "z-line preconditioner needs %.2f GB: %s", (bb + 3 * fb) / 1e9, cudaGetErrorString(e));
   }
   int status = 0;
-  e = cudaMemsetAsync(c->zstatus, 0, sizeof(int), st);
+  e = cudaMemsetAsync(c->zstatus, 0, 2 * sizeof(int), st);
   if (!is_batch(c)) {
     if (e == cudaSuccess) e = tn_zline_setup(c->dm, blk, c->zfac, c->zfac64, c->zstatus, st);
   } else {
@@ -348,11 +348,15 @@ static void free_batch(tn_ctx *c) {
 static bool is_batch(const tn_ctx *c) { return c->batch != nullptr; }
 
 static OpSys make_sys(const tn_ctx *c) {
-  if (is_batch(c)) return c->batch->sys;
   OpSys s;
-  s.m = &c->dm;
-  s.n_apply_parts = c->dm.E;
-  s.n_rz_parts = tn_zline_partials(c->dm);
+  if (is_batch(c)) {
+    s = c->batch->sys;
+  } else {
+    s.m = &c->dm;
+    s.n_apply_parts = c->dm.E;
+    s.n_rz_parts = tn_zline_partials(c->dm);
+  }
+  s.zerr = c->zstatus ? c->zstatus + 1 : nullptr;
   return s;
 }
 
@@ -820,7 +824,6 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   CU_TRY(cudaEventRecord(c->ev_in, c->stream), "event");
   CU_TRY(cudaStreamWaitEvent(s, c->ev_in, 0), "event wait");
   const size_t n = c->ndof;
-  const OpSys sys = make_sys(c);
   if (rhs) CU_TRY(cudaMemcpyAsync(c->b64, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "rhs copy");
   else CU_TRY(make_rhs(c, c->b64, s), "rhs");
   if (!is_batch(c)) CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
@@ -830,7 +833,9 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (zl) {
     tn_status zs = ensure_zline(c, s);
     if (zs != TN_OK) return zs;
+    CU_TRY(cudaMemsetAsync(c->zstatus + 1, 0, sizeof(int), s), "reset");
   }
+  const OpSys sys = make_sys(c);
   tn_solve_report r{};
   tn_status result = TN_OK;
   if (bb == 0.0) {
@@ -962,9 +967,12 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       result = fail(TN_ENOTCONV, "not converged: relative residual %.3e > %.3e after %d iterations",
                     r.rel_residual, o->rtol, r.inner_iters);
   }
+  int zerr = 0;
+  if (zl) CU_TRY(cudaMemcpyAsync(&zerr, c->zstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   CU_TRY(cudaEventRecord(c->ev_out, s), "event");
   CU_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
   CU_TRY(cudaStreamSynchronize(s), "sync");
+  if (zerr && result == TN_OK) result = fail(TN_ETIMEOUT, "a z-line solve gave up waiting for its staged factors");
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   r.status = result;
   r.launches = tn::g_launches;
@@ -987,7 +995,8 @@ tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r,
   if (precond == TN_PC_ZLINE) {
     if ((st = ensure_zline(c, c->stream))) return st;
     CU_TRY(make_sys(c).zsolve(precision, precision == TN_F64 ? (const void *)c->zfac64 : (const void *)c->zfac,
-                              r, z, c->zpart, nullptr, c->stream), "z-line solve");
+                              const_cast<void *>(r), nullptr, z, nullptr, c->zpart, nullptr, c->stream),
+           "z-line solve");
     return TN_OK;
   }
   if (is_batch(c)) return fail(TN_EINVAL, "Jacobi needs a single mesh");

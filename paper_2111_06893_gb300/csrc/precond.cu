@@ -29,9 +29,20 @@ cudaError_t tn_upload_lgl_precond(const LglTables *t) {
 
 namespace {
 
-// factor blocks are padded to a multiple of 4 entries (16-byte aligned for
-// cp.async of float and double blocks)
-__host__ __device__ constexpr int zpad(int M) { return ((M * M + 3) / 4) * 4; }
+// Factor record of one line and slab s: [Linv_s | Z_s].
+//  Linv_s: inverse of the lower Cholesky factor of the slab's Schur
+//          complement, lower triangular, packed column by column (column c
+//          holds rows c..M-1 at zcol(M, c) + (row - c)), M (M + 1) / 2 entries;
+//  Z_s:    L_{s-1}^{-1} O_{s-1}, row-major with an odd row stride zld(M) so
+//          that lanes reading one entry per row hit distinct banks.
+// Both parts are padded to a multiple of 4 entries (16-byte cp.async chunks
+// for float and double records).
+__host__ __device__ constexpr int pad4(int v) { return ((v + 3) / 4) * 4; }
+__host__ __device__ constexpr int zlp(int M) { return pad4(M * (M + 1) / 2); }
+__host__ __device__ constexpr int zld(int M) { return M | 1; }
+__host__ __device__ constexpr int zzp(int M) { return pad4(M * zld(M)); }
+__host__ __device__ constexpr int zrec(int M) { return zlp(M) + zzp(M); }
+__host__ __device__ constexpr int zcol(int M, int c) { return c * M - c * (c - 1) / 2; }
 
 #define LD(a, b) c_lgl_pc.D[N][(a) * N + (b)]
 #define LW(a) c_lgl_pc.w[N][(a)]
@@ -263,183 +274,309 @@ __global__ void zline_factor_kernel(int nlines, int S, double *__restrict__ blk,
       }
     }
     // inverse of the lower-triangular factor (forward substitution on the
-    // identity), stored column-major; Z_s row-major; blocks padded to MP
-    constexpr int MP = zpad(M);
-    float *Lf = fac + (((size_t)line * S + s) * 2 + 0) * MP;
-    double *Ld = fac64 + (((size_t)line * S + s) * 2 + 0) * MP;
+    // identity), packed by columns; Z_s with row stride zld(M)
+    constexpr int LP = zlp(M), LDZ = zld(M), RS = zrec(M);
+    float *Lf = fac + ((size_t)line * S + s) * RS;
+    double *Ld = fac64 + ((size_t)line * S + s) * RS;
     for (int col = 0; col < M; ++col) {
-      for (int r = 0; r < M; ++r) {
+      const int pc = zcol(M, col);
+      for (int r = col; r < M; ++r) {
         double v;
-        if (r < col) v = 0.0;
-        else if (r == col) v = 1.0 / Dm[r * M + r];
-        else {
+        if (r == col) {
+          v = 1.0 / Dm[r * M + r];
+        } else {
           double acc = 0.0;
-          for (int q = col; q < r; ++q) acc += Dm[r * M + q] * Ld[col * M + q];
+          for (int q = col; q < r; ++q) acc += Dm[r * M + q] * Ld[pc + (q - col)];
           v = -acc / Dm[r * M + r];
         }
-        Ld[col * M + r] = v;
-        Lf[col * M + r] = (float)v;
+        Ld[pc + (r - col)] = v;
+        Lf[pc + (r - col)] = (float)v;
       }
     }
-    float *Zf = fac + (((size_t)line * S + s) * 2 + 1) * MP;
-    double *Zd = fac64 + (((size_t)line * S + s) * 2 + 1) * MP;
-    if (s > 0) {
-      const double *Z = blk + (((size_t)line * S + s - 1) * 2 + 1) * M * M;
-      for (int q = 0; q < M * M; ++q) { Zf[q] = (float)Z[q]; Zd[q] = Z[q]; }
-    } else {
-      for (int q = 0; q < M * M; ++q) { Zf[q] = 0.0f; Zd[q] = 0.0; }
+    for (int q = M * (M + 1) / 2; q < LP; ++q) { Lf[q] = 0.0f; Ld[q] = 0.0; }
+    float *Zf = Lf + LP;
+    double *Zd = Ld + LP;
+    const double *Z = s > 0 ? blk + (((size_t)line * S + s - 1) * 2 + 1) * M * M : nullptr;
+    for (int q = 0; q < zzp(M); ++q) {
+      const int r = q / LDZ, col = q - r * LDZ;
+      const double v = (Z && r < M && col < M) ? Z[r * M + col] : 0.0;
+      Zf[q] = (float)v;
+      Zd[q] = v;
     }
   }
 }
 
-// cp.async of one padded block pair (2 MP entries) into shared memory by a warp
-template <typename F, int MP>
-__device__ __forceinline__ void stage_pair(F *dst, const F *src, int lane) {
-  constexpr int CH = (2 * MP * (int)sizeof(F)) / 16;  // 16-byte chunks
-  const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
-  for (int t = lane; t < CH; t += 32)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst + 16 * t), "l"(src + t * (16 / (int)sizeof(F))));
-  asm volatile("cp.async.commit_group;\n" ::);
+// ---- bulk (TMA) copies global -> shared, completion counted on an mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void wait_staged_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void wait_staged_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// one lane: announce `bytes` on bar, then start the copies that deliver them
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// hint: bring `bytes` at src into L2 (no completion to wait for)
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+}
+// wait for the phase with parity `par` of bar to complete; false after the
+// iteration limit (the copy never landed)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned par) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(par)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// shared memory of one warp: two stages of one factor record, two
+// broadcast vectors of 32 entries, two mbarriers
+template <int N, typename F>
+__host__ __device__ constexpr int zline_warp_bytes() {
+  return 2 * zrec(3 * N) * (int)sizeof(F) + 2 * 32 * (int)sizeof(F) + 16;
+}
+template <int N, typename F>
+constexpr size_t zline_smem() { return (size_t)4 * zline_warp_bytes<N, F>(); }
+
+// 16-byte broadcast read of entries c4 .. c4 + 16/sizeof(T) - 1 of a vector
+// that every lane of the warp reads at once
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  static constexpr int W = 4;
+  __device__ static void load(const float *p, float *v) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <> struct Vec16<double> {
+  static constexpr int W = 2;
+  __device__ static void load(const double *p, double *v) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+};
+
+// sum_cc A(cc) x_cc over cc < M with x read from the broadcast vector xv and
+// A(cc) given by `ent` (three partial sums to shorten the dependent chain)
+template <int M, typename T, typename Ent>
+__device__ __forceinline__ T bcast_dot(const T *xv, Ent ent) {
+  constexpr int W = Vec16<T>::W;
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int c4 = 0; c4 < M; c4 += W) {
+    T v[W];
+    Vec16<T>::load(xv + c4, v);
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (c4 + u < M) acc[(c4 + u) % 3] += ent(c4 + u) * v[u];
+  }
+  return (acc[0] + acc[1]) + acc[2];
+}
 
 // z = A_LL^{-1} r on one line (one warp; lane l = a * N + k holds one unknown
-// of a slab).  Forward:  y_s = Linv_s (r_s - Z_s^T y_{s-1});
-// backward:  x_s = Linv_s^T (y_s - Z_{s+1} x_{s+1}).  Every product is a
-// broadcast matrix-vector product (no dependent substitution chain); the
-// slab's blocks are staged in shared memory (two buffers, cp.async) so that
-// global reads are contiguous.  Returns this lane's share of r . z.
-template <int N, typename T, typename F>
-__device__ __forceinline__ T zline_line(const DevMesh &m, const F *__restrict__ fac, const T *__restrict__ r,
-                                        T *__restrict__ z, int line, int lane, F *buf) {
-  constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MP = zpad(M);
+// of a slab), with A_LL = L L^T block-bidiagonal:
+//   forward   y_s = Linv_s (r_s - Z_s^T y_{s-1})      (y = L^{-1} r, kept in z)
+//   backward  x_s = Linv_s^T (y_s - Z_{s+1} x_{s+1})  (x = L^{-T} y)
+// Every product is a broadcast matrix-vector product.  The factor record of
+// the next slab is brought into shared memory by one bulk copy while the
+// current slab is worked on (two stages); this lane's r, q and y entries are
+// loaded two slabs ahead into registers.  UPD: first r <- r - alpha q (the
+// PCG residual update, written back).  Adds this lane's r.z (= |y|^2, since
+// r.z = r^T L^-T L^-1 r) and r.r to rz, rr.  A staging wait that runs out
+// sets *err and ends the line.
+template <int N, typename T, typename F, bool UPD>
+__device__ __forceinline__ void zline_line(const DevMesh &m, const F *__restrict__ fac, T *__restrict__ r,
+                                           const T *__restrict__ q, T *__restrict__ z, T alpha, int line,
+                                           int lane, unsigned char *smem, int *err, T &rz, T &rr) {
+  static_assert(sizeof(T) == sizeof(F), "vectors and factors share one precision");
+  constexpr int M = 3 * N, N2 = N * N, n = N * N * N;
+  constexpr int LP = zlp(M), LDZ = zld(M), RS = zrec(M);
   const int S = m.nslab;
-  T rzt = T(0);
-  const int c = line / N2, q = line - c * N2, i = q % N, j = q / N;
+  const int c = line / N2, qn = line - c * N2, i = qn % N, j = qn / N;
   const int a = lane / N, k = lane - (lane / N) * N;
   const bool act = lane < M;
   const int ll = act ? lane : 0;
   const size_t off = (size_t)k * N2 + j * N + i;
-  const F *base = fac + (size_t)line * S * 2 * MP;  // slab s: [Linv_s | Z_s]
+  const size_t ncol = m.ncol;
+  const F *base = fac + (size_t)line * S * RS;
+  F *const stg0 = reinterpret_cast<F *>(smem);
+  T *const vb = reinterpret_cast<T *>(smem + 2 * RS * sizeof(F));  // b_s / y_s (broadcast)
+  T *const vx = vb + 32;                                            // y_{s-1} / x_{s+1} (broadcast)
+  unsigned long long *const bar =
+      reinterpret_cast<unsigned long long *>(smem + 2 * RS * sizeof(F) + 64 * sizeof(F));
+  unsigned ph = 0u, pend = 0u;  // bit b: phase parity / copy in flight of stage b
+  auto stg = [&](int b) { return stg0 + b * RS; };
+  auto gidx = [&](int s) { return ((size_t)(s * ncol + c) * 3 + (act ? a : 0)) * n + off; };
+  auto issue = [&](int b, const F *src0, int cnt0, const F *src1, int cnt1) {
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect(bar + b, (unsigned)((cnt0 + cnt1) * sizeof(F)));
+      bulk_g2s(stg(b), src0, (unsigned)(cnt0 * sizeof(F)), bar + b);
+      if (cnt1) bulk_g2s(stg(b) + LP, src1, (unsigned)(cnt1 * sizeof(F)), bar + b);
+    }
+    pend |= 1u << b;
+  };
+  auto wait = [&](int b) {
+    const bool ok = mbar_wait(bar + b, (ph >> b) & 1u);
+    ph ^= 1u << b;
+    pend &= ~(1u << b);
+    return ok;
+  };
+  auto drain = [&]() {  // after a timeout: give the copies still in flight a bounded wait
+    if (pend & 1u) wait(0);
+    if (pend & 2u) wait(1);
+    if (lane == 0 && err) atomicExch(err, 1);
+  };
+  if (lane == 0) {
+    mbar_init(bar);
+    mbar_init(bar + 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
   // forward sweep
-  stage_pair<F, MP>(buf, base, lane);
+  issue(0, base, RS, nullptr, 0);
+  T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
+  T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
   T yprev = T(0);
+  if (lane == 0 && S > 1) bulk_prefetch_l2(base + RS, RS * sizeof(F));
   for (int s = 0; s < S; ++s) {
-    F *cur = buf + (s & 1) * 2 * MP;
-    if (s + 1 < S) {
-      stage_pair<F, MP>(buf + ((s + 1) & 1) * 2 * MP, base + (size_t)(s + 1) * 2 * MP, lane);
-      wait_staged_all_but_one();
-    } else {
-      wait_staged_all();
+    const int b = s & 1;
+    // the record two slabs ahead goes to L2 now, so that its bulk copy (issued
+    // at the next step) is served from L2
+    if (lane == 0 && s + 2 < S) bulk_prefetch_l2(base + (size_t)(s + 2) * RS, RS * sizeof(F));
+    if (s + 1 < S) issue(b ^ 1, base + (size_t)(s + 1) * RS, RS, nullptr, 0);
+    if (!wait(b)) { drain(); return; }
+    const F *Li = stg(b), *Zs = stg(b) + LP;
+    const size_t idx = gidx(s);
+    T rv = r0;
+    if (UPD) {
+      rv -= alpha * q0;
+      if (act) r[idx] = rv;
     }
+    // entries two slabs ahead
+    r0 = r1;
+    q0 = q1;
+    if (act && s + 2 < S) {
+      r1 = r[gidx(s + 2)];
+      if (UPD) q1 = q[gidx(s + 2)];
+    }
+    rr += rv * rv;
+    T bv = rv;
+    if (s > 0) bv -= bcast_dot<M, T>(vx, [&](int cc) { return (T)Zs[cc * LDZ + ll]; });  // Z_s^T y_{s-1}
+    vb[lane] = act ? bv : T(0);
     __syncwarp();
-    const F *Li = cur, *Zs = cur + MP;
-    const size_t e = (size_t)s * m.ncol + c;
-    const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
-    T b = act ? r[idx] : T(0);
-    if (s > 0) {
-#pragma unroll
-      for (int cc = 0; cc < M; ++cc) b -= (T)Zs[cc * M + ll] * __shfl_sync(0xffffffffu, yprev, cc);
-    }
-    T y = T(0);
-#pragma unroll
-    for (int cc = 0; cc < M; ++cc) y += (T)Li[cc * M + ll] * __shfl_sync(0xffffffffu, b, cc);
+    T y = bcast_dot<M, T>(vb, [&](int cc) { return cc <= ll ? (T)Li[zcol(M, cc) + ll - cc] : T(0); });
     if (!act) y = T(0);
+    rz += y * y;
     if (act) z[idx] = y;
     yprev = y;
-    __syncwarp();  // buffer (s & 1) is restaged two slabs later
+    __syncwarp();  // every lane is done with vx, vb and stage b
+    vx[lane] = y;
+    __syncwarp();
   }
   // backward sweep: slab s needs Linv_s and Z_{s+1}
-  T xn = T(0);
-  for (int s = S - 1; s >= 0; --s) {
-    const F *Li = base + (size_t)s * 2 * MP;
-    F *cur = buf;
-    // stage Linv_s (first half of pair s) and Z_{s+1} (second half of pair s+1)
-    {
-      constexpr int CH = (MP * (int)sizeof(F)) / 16;
-      const unsigned d0 = (unsigned)__cvta_generic_to_shared(cur);
-      const unsigned d1 = (unsigned)__cvta_generic_to_shared(cur + MP);
-      for (int t = lane; t < CH; t += 32)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d0 + 16 * t), "l"(Li + t * (16 / (int)sizeof(F))));
-      if (s + 1 < S) {
-        const F *Zn = base + (size_t)(s + 1) * 2 * MP + MP;
-        for (int t = lane; t < CH; t += 32)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d1 + 16 * t), "l"(Zn + t * (16 / (int)sizeof(F))));
-      }
-      asm volatile("cp.async.commit_group;\n" ::);
-      wait_staged_all();
-    }
+  auto issue_bwd = [&](int s, int b) {
+    issue(b, base + (size_t)s * RS, LP, base + (size_t)(s + 1) * RS + LP, s + 1 < S ? RS - LP : 0);
+  };
+  const int pl = zcol(M, ll) - ll;
+  int bb = S & 1;  // the stage the forward sweep did not end on
+  issue_bwd(S - 1, bb);
+  T y0 = yprev;  // y_{S-1}
+  T y1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
+  T y2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
+  if (lane == 0 && S > 1) bulk_prefetch_l2(base + (size_t)(S - 2) * RS, RS * sizeof(F));
+  for (int s = S - 1; s >= 0; --s, bb ^= 1) {
+    if (lane == 0 && s >= 2) bulk_prefetch_l2(base + (size_t)(s - 2) * RS, RS * sizeof(F));
+    if (s > 0) issue_bwd(s - 1, bb ^ 1);
+    if (!wait(bb)) { drain(); return; }
+    const F *Li = stg(bb), *Zn = stg(bb) + LP;
+    T yv = y0;
+    y0 = y1;
+    y1 = y2;
+    if (act && s >= 3) y2 = z[gidx(s - 3)];
+    if (s + 1 < S) yv -= bcast_dot<M, T>(vx, [&](int cc) { return (T)Zn[ll * LDZ + cc]; });  // Z_{s+1} x_{s+1}
+    vb[lane] = act ? yv : T(0);
     __syncwarp();
-    const size_t e = (size_t)s * m.ncol + c;
-    const size_t idx = (e * 3 + (act ? a : 0)) * n + off;
-    T yv = act ? z[idx] : T(0);
-    if (s < S - 1) {
-      const F *Zs = cur + MP;
-#pragma unroll
-      for (int cc = 0; cc < M; ++cc) yv -= (T)Zs[ll * M + cc] * __shfl_sync(0xffffffffu, xn, cc);
-    }
-    T x = T(0);
-#pragma unroll
-    for (int cc = 0; cc < M; ++cc) x += (T)cur[ll * M + cc] * __shfl_sync(0xffffffffu, yv, cc);
+    T x = bcast_dot<M, T>(vb, [&](int cc) { return cc >= ll ? (T)Li[pl + cc] : T(0); });
     if (!act) x = T(0);
-    if (act) {
-      z[idx] = x;
-      rzt += r[idx] * x;
-    }
-    xn = x;
+    if (act) z[gidx(s)] = x;
+    __syncwarp();  // every lane is done with vx, vb and stage bb
+    vx[lane] = x;
     __syncwarp();
   }
-  return rzt;
 }
 
-// four lines (warps) per block; partial sums of r . z per block
-__device__ __forceinline__ void block_partial_rz(double rz, double *part) {
-  __shared__ double red[4];
+// four lines (warps) per block; per-block partial sums of r.z and r.r
+__device__ __forceinline__ void block_partial2(double rz, double rr, double *part_rz, double *part_rr) {
+  __shared__ double red[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
-  if (lane == 0) red[warp] = rz;
+  for (int o = 16; o > 0; o >>= 1) {
+    rz += __shfl_xor_sync(0xffffffffu, rz, o);
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  }
+  if (lane == 0) { red[warp] = rz; red[4 + warp] = rr; }
   __syncthreads();
-  if (threadIdx.x == 0 && part) part[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  if (threadIdx.x == 0) {
+    if (part_rz) part_rz[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+    if (part_rr) part_rr[blockIdx.x] = red[4] + red[5] + red[6] + red[7];
+  }
 }
 
-template <int N, typename F>
-constexpr size_t zline_smem() { return sizeof(F) * 4 * 2 * 2 * zpad(3 * N); }
-
-template <int N, typename T, typename F>
+template <int N, typename T, typename F, bool UPD>
 __global__ void __launch_bounds__(128)
-zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, const T *__restrict__ r, T *__restrict__ z,
-                   double *__restrict__ part, const int *__restrict__ done) {
+zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
+                   T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
+                   double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char zsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  F *buf = reinterpret_cast<F *>(zsm) + warp * 4 * zpad(3 * N);
   const int line = blockIdx.x * 4 + warp;
-  T rzt = T(0);
-  if (line < m.ncol * N * N) rzt = zline_line<N, T, F>(m, fac, r, z, line, lane, buf);
-  block_partial_rz((double)rzt, part);
+  const T al = UPD ? (T)*alpha : T(0);
+  T rz = T(0), rr = T(0);
+  if (line < m.ncol * N * N)
+    zline_line<N, T, F, UPD>(m, fac, r, q, z, al, line, lane, zsm + warp * zline_warp_bytes<N, F>(), err, rz,
+                             rr);
+  block_partial2((double)rz, (double)rr, part_rz, part_rr);
 }
 
 // a batch: warp w of block b handles line work[4 b + w] = (instance, line)
-template <int N, typename T, typename F>
+template <int N, typename T, typename F, bool UPD>
 __global__ void __launch_bounds__(128)
 zline_solve_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work, int nwork,
                          const long long *__restrict__ fac_off, const long long *__restrict__ dof_off,
-                         const F *__restrict__ fac, const T *__restrict__ r, T *__restrict__ z,
-                         double *__restrict__ part, const int *__restrict__ done) {
+                         const F *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
+                         T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
+                         double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char zsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  F *buf = reinterpret_cast<F *>(zsm) + warp * 4 * zpad(3 * N);
   const int wi = blockIdx.x * 4 + warp;
-  T rzt = T(0);
+  const T al = UPD ? (T)*alpha : T(0);
+  T rz = T(0), rr = T(0);
   if (wi < nwork) {
     const int2 w = work[wi];
     const long long off = dof_off[w.x];
-    rzt = zline_line<N, T, F>(meshes[w.x], fac + fac_off[w.x], r + off, z + off, w.y, lane, buf);
+    zline_line<N, T, F, UPD>(meshes[w.x], fac + fac_off[w.x], r + off, UPD ? q + off : nullptr, z + off, al,
+                             w.y, lane, zsm + warp * zline_warp_bytes<N, F>(), err, rz, rr);
   }
-  block_partial_rz((double)rzt, part);
+  block_partial2((double)rz, (double)rr, part_rz, part_rr);
 }
 
 template <int N>
@@ -459,22 +596,57 @@ cudaError_t zline_smem_optin(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N>
-cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, const void *r, void *z, double *part,
-                    const int *done, cudaStream_t st) {
-  const int nlines = m.ncol * N * N;
-  const int blocks = (nlines + 3) / 4;
-  cudaError_t err = prec == TN_F64
-                        ? zline_smem_optin(zline_solve_kernel<N, double, double>, zline_smem<N, double>())
-                        : zline_smem_optin(zline_solve_kernel<N, float, float>, zline_smem<N, float>());
+template <int N, typename T, bool UPD>
+cudaError_t solve_nt(const DevMesh &m, const void *fac, void *r, const void *q, void *z, const double *alpha,
+                     double *part_rz, double *part_rr, const int *done, int *zerr, cudaStream_t st) {
+  const int blocks = (m.ncol * N * N + 3) / 4;
+  constexpr size_t sm = zline_smem<N, T>();
+  cudaError_t err = zline_smem_optin(zline_solve_kernel<N, T, T, UPD>, sm);
   if (err != cudaSuccess) return err;
-  if (prec == TN_F64)
-    zline_solve_kernel<N, double, double><<<blocks, 128, zline_smem<N, double>(), st>>>(
-        m, (const double *)fac, (const double *)r, (double *)z, part, done);
-  else
-    zline_solve_kernel<N, float, float><<<blocks, 128, zline_smem<N, float>(), st>>>(
-        m, (const float *)fac, (const float *)r, (float *)z, part, done);
+  zline_solve_kernel<N, T, T, UPD><<<blocks, 128, sm, st>>>(m, (const T *)fac, (T *)r, (const T *)q, (T *)z,
+                                                             alpha, part_rz, part_rr, done, zerr);
   return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
+                    const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                    cudaStream_t st) {
+  if (prec == TN_F64)
+    return q ? solve_nt<N, double, true>(m, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st)
+             : solve_nt<N, double, false>(m, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st);
+  return q ? solve_nt<N, float, true>(m, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st)
+           : solve_nt<N, float, false>(m, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st);
+}
+
+template <int N, typename T, bool UPD>
+cudaError_t solve_batch_nt(const DevMesh *meshes, const int2 *work, int nwork, const long long *fac_off,
+                           const long long *dof_off, const void *fac, void *r, const void *q, void *z,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           cudaStream_t st) {
+  constexpr size_t sm = zline_smem<N, T>();
+  cudaError_t err = zline_smem_optin(zline_solve_batch_kernel<N, T, T, UPD>, sm);
+  if (err != cudaSuccess) return err;
+  zline_solve_batch_kernel<N, T, T, UPD><<<(nwork + 3) / 4, 128, sm, st>>>(
+      meshes, work, nwork, fac_off, dof_off, (const T *)fac, (T *)r, (const T *)q, (T *)z, alpha, part_rz,
+      part_rr, done, zerr);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t solve_batch_n(int prec, const DevMesh *meshes, const int2 *work, int nwork, const long long *fac_off,
+                          const long long *dof_off, const void *fac, void *r, const void *q, void *z,
+                          const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                          cudaStream_t st) {
+  if (prec == TN_F64)
+    return q ? solve_batch_nt<N, double, true>(meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha,
+                                               part_rz, part_rr, done, zerr, st)
+             : solve_batch_nt<N, double, false>(meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha,
+                                                part_rz, part_rr, done, zerr, st);
+  return q ? solve_batch_nt<N, float, true>(meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha, part_rz,
+                                            part_rr, done, zerr, st)
+           : solve_batch_nt<N, float, false>(meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha,
+                                             part_rz, part_rr, done, zerr, st);
 }
 
 }  // namespace
@@ -485,7 +657,7 @@ size_t tn_zline_block_bytes(const DevMesh &m) {
 }
 
 size_t tn_zline_factor_entries(const DevMesh &m) {
-  return (size_t)m.ncol * m.N * m.N * m.nslab * 2 * zpad(3 * m.N);
+  return (size_t)m.ncol * m.N * m.N * m.nslab * zrec(3 * m.N);
 }
 
 size_t tn_zline_factor_bytes(const DevMesh &m) { return tn_zline_factor_entries(m) * sizeof(float); }
@@ -506,41 +678,28 @@ cudaError_t tn_zline_setup(const DevMesh &m, double *blk, float *fac, double *fa
   }
 }
 
-cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, const void *r, void *z, double *part,
-                           const int *done, cudaStream_t st) {
+cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           cudaStream_t st) {
   switch (m.N) {
-    case 3: return solve_n<3>(m, prec, fac, r, z, part, done, st);
-    case 4: return solve_n<4>(m, prec, fac, r, z, part, done, st);
-    case 5: return solve_n<5>(m, prec, fac, r, z, part, done, st);
-    case 6: return solve_n<6>(m, prec, fac, r, z, part, done, st);
-    case 7: return solve_n<7>(m, prec, fac, r, z, part, done, st);
-    case 8: return solve_n<8>(m, prec, fac, r, z, part, done, st);
-    case 9: return solve_n<9>(m, prec, fac, r, z, part, done, st);
+#define TN_CASE(NN) \
+    case NN: return solve_n<NN>(m, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st);
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const int2 *work, int nwork,
-                                 const long long *fac_off, const long long *dof_off, const void *fac,
-                                 const void *r, void *z, double *part, const int *done, cudaStream_t st) {
+                                 const long long *fac_off, const long long *dof_off, const void *fac, void *r,
+                                 const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
+                                 const int *done, int *zerr, cudaStream_t st) {
   if (nwork <= 0) return cudaSuccess;
-  const int blocks = (nwork + 3) / 4;
   switch (N) {
-#define TN_CASE(NN)                                                                                       \
-  case NN:                                                                                               \
-    {                                                                                                    \
-      cudaError_t oe = prec == TN_F64                                                                    \
-          ? zline_smem_optin(zline_solve_batch_kernel<NN, double, double>, zline_smem<NN, double>())     \
-          : zline_smem_optin(zline_solve_batch_kernel<NN, float, float>, zline_smem<NN, float>());       \
-      if (oe != cudaSuccess) return oe;                                                                  \
-    }                                                                                                    \
-    if (prec == TN_F64)                                                                                  \
-      zline_solve_batch_kernel<NN, double, double><<<blocks, 128, zline_smem<NN, double>(), st>>>(      \
-          meshes, work, nwork, fac_off, dof_off, (const double *)fac, (const double *)r, (double *)z, part, done); \
-    else                                                                                                 \
-      zline_solve_batch_kernel<NN, float, float><<<blocks, 128, zline_smem<NN, float>(), st>>>(          \
-          meshes, work, nwork, fac_off, dof_off, (const float *)fac, (const float *)r, (float *)z, part, done);    \
-    return cudaGetLastError();
+#define TN_CASE(NN)                                                                                   \
+    case NN:                                                                                         \
+      return solve_batch_n<NN>(prec, meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha, part_rz, \
+                               part_rr, done, zerr, st);
     TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
     default: return cudaErrorInvalidValue;

@@ -2,19 +2,22 @@
 //
 // The paper solves with GMRES; the weak-form DG operator built here is
 // symmetric positive definite, so the solver is preconditioned conjugate
-// gradients (Jacobi).  Each iteration is five launches -- the fused operator
-// apply (which also returns p.Ap per element), a one-block reduction for
-// alpha, a fused vector update (x, r, z = D^-1 r, partial r.z and r.r), a
-// one-block reduction for beta and the direction update -- recorded once in
-// a CUDA graph of `chunk` iterations and replayed.  Krylov scalars live on
-// the device; once converged every kernel returns immediately, so a replayed
-// chunk never runs past convergence.  The host reads a small status block
-// after each chunk.  Reductions use a fixed partition and a fixed order, so
-// results are bitwise reproducible.
+// gradients.  With the Jacobi preconditioner an iteration is five launches:
+// the fused operator apply (which also returns p.Ap per element), a
+// one-block reduction for alpha, a fused vector update (x, r, z = D^-1 r,
+// partial r.z and r.r), a one-block reduction for beta and the direction
+// update.  With the column-line preconditioner the residual update r -= alpha
+// q runs inside the line solve (which also returns partial r.z and r.r) and
+// the solution update x += alpha p inside the direction update.  A chunk of
+// iterations is recorded once in a CUDA graph and replayed.  Krylov scalars
+// live on the device; once converged every kernel returns immediately, so a
+// replayed chunk never runs past convergence.  The host reads a small status
+// block after each chunk.  Reductions use a fixed partition and a fixed
+// order, so results are bitwise reproducible.
 //
-// Mixed precision: iterative refinement with the FP64 residual b - A x and
-// FP64 update, inner PCG entirely in FP32 (vectors, operator, diagonal),
-// scalars in FP64.
+// Mixed precision: a flexible CG in FP64 (residual, update, directions)
+// preconditioned by a fixed number of FP32 PCG iterations (vectors,
+// operator, line factors), scalars in FP64.
 #include <cmath>
 #include <cstring>
 
@@ -59,9 +62,13 @@ __device__ double block_sum_array(const double *v, int n) {
 }
 
 __global__ void k_alpha(tn_pcg_scalars *s, const double *partial, int n) {
-  if (s->done) return;
+  if (s->done) {
+    if (threadIdx.x == 0) s->active = 0;
+    return;
+  }
   const double pq = block_sum_array(partial, n);
   if (threadIdx.x == 0) {
+    s->active = 1;
     s->pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {
       s->breakdown = 1;
@@ -167,6 +174,7 @@ __global__ void k_init_scalars(tn_pcg_scalars *s, const double *part, int nb, do
     s->max_iters = max_iters;
     s->breakdown = 0;
     s->done = (rr == 0.0 || rr <= s->tol2) ? 1 : 0;
+    s->active = 0;
     s->alpha = s->beta = s->pq = 0.0;
   }
 }
@@ -291,23 +299,6 @@ __global__ void k_upcast(size_t n, const float *__restrict__ d, double scale, do
 }
 
 // ---- variants for a preconditioner applied by a separate kernel (z-line)
-template <typename T>
-__global__ void k_update_r(tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__restrict__ r,
-                           const T *__restrict__ p, const T *__restrict__ q, double *part) {
-  if (s->done) return;
-  const T alpha = (T)s->alpha;
-  T rrt = T(0);
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    x[t] += alpha * p[t];
-    const T rv = r[t] - alpha * q[t];
-    r[t] = rv;
-    rrt += rv * rv;
-  }
-  double rr = (double)rrt, dummy = 0.0;
-  block_sum2(rr, dummy);
-  if (threadIdx.x == 0) part[blockIdx.x] = rr;
-}
-
 __device__ void finish_beta(tn_pcg_scalars *s, double rz, double rr) {
   s->iters += 1;
   s->rr = rr;
@@ -328,6 +319,22 @@ __global__ void k_beta_split(tn_pcg_scalars *s, const double *rzp, int nrz, cons
   for (int t = threadIdx.x; t < nrr; t += blockDim.x) rr += rrp[t];
   block_sum2(rz, rr);
   if (threadIdx.x == 0) finish_beta(s, rz, rr);
+}
+
+// x += alpha p (the iteration's solution update, deferred to here so that
+// the residual update can run inside the line solve), then p = z + beta p
+// unless the run has just finished
+template <typename T>
+__global__ void k_pupdate_x(const tn_pcg_scalars *s, size_t n, T *__restrict__ x, T *__restrict__ p,
+                            const T *__restrict__ z) {
+  if (!s->active) return;
+  const T alpha = (T)s->alpha, beta = (T)s->beta;
+  const bool more = !s->done;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const T pv = p[t];
+    x[t] += alpha * pv;
+    if (more) p[t] = z[t] + beta * pv;
+  }
 }
 
 // r = b - Ax (or b), partial r.r
@@ -365,6 +372,7 @@ __global__ void k_init_scalars_split(tn_pcg_scalars *s, const double *rzp, int n
     s->max_iters = max_iters;
     s->breakdown = 0;
     s->done = (rr == 0.0 || rr <= s->tol2) ? 1 : 0;
+    s->active = 0;
     s->alpha = s->beta = s->pq = 0.0;
   }
 }
@@ -412,13 +420,11 @@ static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, Pcg
   TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
   k_alpha<<<1, 256, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
-  k_update_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (const T *)v.p, (const T *)v.q,
-                                                    part_red);
+  // r -= alpha q fused into the line solve (partials r.z and r.r)
+  TN_CU(sys.zsolve(prec, v.zfac, v.r, v.q, v.z, &s->alpha, v.part_rz, &s->done, st));
+  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts, sys.n_rz_parts);
   TN_CU(cudaGetLastError());
-  TN_CU(sys.zsolve(prec, v.zfac, v.r, v.z, v.part_rz, &s->done, st));
-  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, sys.n_rz_parts, part_red, kRedBlocks);
-  TN_CU(cudaGetLastError());
-  k_pupdate<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
+  k_pupdate_x<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
 }
 
@@ -430,7 +436,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
                            double *part_elem, double *part_red, cudaStream_t st, int *applies,
                            ChunkHook hook = ChunkHook()) {
   const bool zl = v.zfac != nullptr;
-  g_launches += zl ? 6 : 3;
+  g_launches += zl ? 5 : 3;
   if (x0_zero) {
     k_fill<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.x, T(0));
     TN_CU(cudaGetLastError());
@@ -442,11 +448,11 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   if (zl) {
     k_init_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, part_red);
     TN_CU(cudaGetLastError());
-    TN_CU(sys.zsolve(prec, v.zfac, v.r, v.z, v.part_rz, nullptr, st));
+    TN_CU(sys.zsolve(prec, v.zfac, v.r, nullptr, v.z, nullptr, v.part_rz, nullptr, st));
     k_copy<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.p, (const T *)v.z);
     TN_CU(cudaGetLastError());
-    k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, sys.n_rz_parts, part_red, kRedBlocks,
-                                            rtol * rtol, max_iters);
+    k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts,
+                                            sys.n_rz_parts, rtol * rtol, max_iters);
   } else {
     k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, (T *)v.z, (T *)v.p,
                                                   (const T *)v.dinv, part_red);
@@ -506,7 +512,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   double best = INFINITY;
   int stall = 0;
   for (;;) {
-    g_launches += (zl ? 6LL : 5LL) * chunk;
+    g_launches += 5LL * chunk;
     err = cudaGraphLaunch(exec, st);
     if (err != cudaSuccess) break;
     err = cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st);
@@ -599,12 +605,14 @@ cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStr
   return cudaSuccess;
 }
 
-cudaError_t OpSys::zsolve(int prec, const void *fac, const void *r, void *z, double *part, const int *done,
-                          cudaStream_t st) const {
-  if (m) return tn_zline_solve(*m, prec, fac, r, z, part, done, st);
+cudaError_t OpSys::zsolve(int prec, const void *fac, void *r, const void *q, void *z, const double *alpha,
+                          double *part, const int *done, cudaStream_t st) const {
+  double *prr = part ? part + n_rz_parts : nullptr;
+  if (m) return tn_zline_solve(*m, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
   for (int g = 0; g < ngroups; ++g) {
-    cudaError_t e = tn_zline_solve_batch(gN[g], prec, meshes, gline[g], glines[g], fac_off, dof_off, fac, r, z,
-                                         part ? part + grz_off[g] : nullptr, done, st);
+    cudaError_t e = tn_zline_solve_batch(gN[g], prec, meshes, gline[g], glines[g], fac_off, dof_off, fac, r, q, z,
+                                         alpha, part ? part + grz_off[g] : nullptr,
+                                         prr ? prr + grz_off[g] : nullptr, done, zerr, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -8,15 +8,21 @@
 
 size_t tn_zline_block_bytes(const DevMesh &m);   // FP64 set-up blocks
 size_t tn_zline_factor_bytes(const DevMesh &m);  // FP32 factors kept for the solve
-size_t tn_zline_factor_entries(const DevMesh &m);  // entries per precision (padded blocks)
-int tn_zline_partials(const DevMesh &m);         // partial sums written by one solve
+size_t tn_zline_factor_entries(const DevMesh &m);  // entries per precision (padded records)
+int tn_zline_partials(const DevMesh &m);         // partial sums of r.z (and of r.r) written by one solve
 cudaError_t tn_zline_setup(const DevMesh &m, double *blk, float *fac, double *fac64, int *status,
                            cudaStream_t st);
-cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, const void *r, void *z, double *part,
-                           const int *done, cudaStream_t st);
+// z = M^{-1} r with M the column-line blocks; q != nullptr: first
+// r <- r - (*alpha) q (written back).  Per block of four lines: part_rz[b] =
+// partial r.z, part_rr[b] = partial r.r (either may be nullptr).  *done != 0:
+// returns at once.  A staging wait that runs out sets *zerr = 1.
+cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           cudaStream_t st);
 cudaError_t tn_upload_lgl_precond(const LglTables *t);
 // batch: warp w of block b solves line work[4 b + w] = (instance, line); factors of
 // instance i at fac + fac_off[i] (elements of the factor type), vectors at dof_off[i]
 cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const int2 *work, int nwork,
-                                 const long long *fac_off, const long long *dof_off, const void *fac,
-                                 const void *r, void *z, double *part, const int *done, cudaStream_t st);
+                                 const long long *fac_off, const long long *dof_off, const void *fac, void *r,
+                                 const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
+                                 const int *done, int *zerr, cudaStream_t st);

@@ -10,6 +10,7 @@
 struct tn_pcg_scalars {
   double rz, rr, rr0, pq, alpha, beta, tol2;
   int iters, max_iters, done, breakdown;
+  int active;  // the current iteration ran (set by the alpha step)
 };
 
 // the operator and preconditioner of a solve: one mesh, or a batch of meshes
@@ -27,10 +28,13 @@ struct OpSys {
   int grz_off[8] = {0};
   const long long *dof_off = nullptr, *fac_off = nullptr;
   int n_apply_parts = 0;  // partial sums written by one apply
-  int n_rz_parts = 0;     // partial sums written by one z-line solve
+  int n_rz_parts = 0;     // partial sums of r.z written by one z-line solve (r.r: as many, after them)
+  int *zerr = nullptr;    // set to 1 by a z-line solve whose staging wait ran out
   cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const;
-  cudaError_t zsolve(int prec, const void *fac, const void *r, void *z, double *part, const int *done,
-                     cudaStream_t st) const;
+  // z = M^{-1} r; q != nullptr: first r <- r - (*alpha) q.  part: n_rz_parts
+  // partial r.z, then n_rz_parts partial r.r
+  cudaError_t zsolve(int prec, const void *fac, void *r, const void *q, void *z, const double *alpha,
+                     double *part, const int *done, cudaStream_t st) const;
 };
 
 // vectors of one PCG run, all of the run's precision
@@ -38,7 +42,7 @@ struct PcgVectors {
   void *x, *r, *z, *p, *q;
   const void *b, *dinv;
   const void *zfac = nullptr;   // z-line factors of the run's precision (nullptr: Jacobi)
-  double *part_rz = nullptr;    // partial r.z of the z-line solve
+  double *part_rz = nullptr;    // partial r.z and r.r of the z-line solve (2 n_rz_parts)
 };
 
 cudaError_t tn_jacobi_apply(size_t n, int prec, const double *diag, const void *r, void *z, cudaStream_t st);
