@@ -9,8 +9,9 @@ are resident in HBM before the timed region; L2 is flushed between steps.
 
 metric: GDOF/s = (operator applies x N_DOF) / time, over the whole step.
 Extra keys report the FP32/FP64 apply kernels alone, the time to U for the
-mixed and the plain FP64 solve, the roofline of the dominant kernel and the
-FP64 oracle on the host cores.
+mixed and the plain FP64 solve, the roofline of the dominant kernel of the
+step (the FP32 column-line solve, HBM-bound) and of the FP32 apply
+(ALU-bound), and the FP64 oracle on the host cores.
 
 Multi-GPU: replicas only (every rank solves its own mirror; no collective on
 the data path); value = all ranks' DOF-applies / max over ranks of the time.
@@ -51,6 +52,24 @@ def fp32_apply_flops_per_dof(N):
     terms (~130 + 18 N)."""
     per_elem = N ** 3 * (36 * N + 80) + 6 * N ** 2 * (130 + 18 * N)
     return per_elem / (3 * N ** 3)
+
+
+def zline_factor_bytes(d):
+    """FP32 bytes of the column-line factors of one mirror: per line (column
+    x cross-section node) and slab, the packed inverse diagonal factor
+    M (M + 1) / 2 and the coupling block M x (M | 1), each padded to 4 entries
+    (M = 3 N)."""
+    N = d["degree"] + 1
+    M = 3 * N
+    pad4 = lambda v: (v + 3) // 4 * 4
+    rec = pad4(M * (M + 1) // 2) + pad4(M * (M | 1))
+    return W.n_columns(d) * N * N * (len(d["slab_z"]) - 1) * rec * 4
+
+
+# DRAM bytes (read + write) of one z-line solve launch (no residual update),
+# from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of
+# `bench.py --mode apply`; absent where no capture of the current kernel exists
+ZLINE_TRAFFIC = {}
 
 
 def measured_peaks():
@@ -365,6 +384,22 @@ def main():
 
     t32 = time_apply(x32, y32, 200)
     t64 = time_apply(x64, y64, 20)
+
+    # the dominant kernel of the step: the FP32 column-line solve
+    def time_zline(x, y, reps_n):
+        for _ in range(5):
+            ctx.precond_apply(x, y, precond="zline")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps_n):
+            ctx.precond_apply(x, y, precond="zline")
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps_n / 1e3
+
+    tz = time_zline(x32, y32, 100)
+    zbytes = sum(zline_factor_bytes(d) for d in descs) + 8 * ndof  # factors once, r in, z out
     flops = flops_dof * ndof
     sm_max = 2070.0
     peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
@@ -409,6 +444,10 @@ def main():
                "sample": f"{done} element rows of A u of this workload by the FP64 oracle "
                          f"(explicit element matrices), {dt:.1f} s"}
     clocks = clk.summary()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+    zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
+               else f"zline_solve_kernel<{N},float,float,0>")
     line = {
         "metric": "GDOF/s of DG elasticity apply", "value": value, "unit": "GDOF/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -434,13 +473,17 @@ def main():
                   "reference_status": rep_ref["status"]},
         "apply_kernel": {"f32_us": t32 * 1e6, "f64_us": t64 * 1e6,
                          "f32_gdofs": ndof / t32 / 1e9, "f64_gdofs": ndof / t64 / 1e9},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": "apply2_batch_kernel<N,float>" if batched else f"apply2_kernel<{N},float>",
-                     "flops_per_dof": flops_dof,
-                     "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
-                     "hbm_peak_GBps": peaks.get("hbm_gbs"),
-                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
+        "roofline": {"bound": "hbm", "achieved": zbytes / tz / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": zbytes / tz / 1e9 / hbm_peak,
+                     "traffic": ZLINE_TRAFFIC.get((args.workload, zkernel)),
+                     "kernel": zkernel, "us": tz * 1e6, "algorithmic_bytes": zbytes,
+                     "peak_source": peak_src},
+        "roofline_apply": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                           "frac": achieved / peak_fp32, "traffic": None,
+                           "kernel": "apply2_batch_kernel<N,float>" if batched else f"apply2_kernel<{N},float>",
+                           "flops_per_dof": flops_dof,
+                           "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
+                           "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "seconds": e2e_times[-1][0]},
         "gpu_launches": launches,
