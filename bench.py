@@ -212,7 +212,7 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--inner-max", type=int, default=300)
     ap.add_argument("--fcg-window", type=int, default=16)
-    ap.add_argument("--precond", default="zline", choices=["zline", "jacobi"])
+    ap.add_argument("--precond", default="zline", choices=["zline", "zgroup", "jacobi"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-U solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-reference", action="store_true",
@@ -275,17 +275,18 @@ def main():
             res[name] = e0.elapsed_time(e1) / reps_n * 1e3
         # the column-line preconditioner solve (one launch per application)
         zres = {}
-        for name, x, y, reps_n in (("f32", x32, y32, 20), ("f64", x64, y64, 10)):
-            for _ in range(3):
-                ctx.precond_apply(x, y, precond="zline")
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps_n):
-                ctx.precond_apply(x, y, precond="zline")
-            e1.record(stream)
-            e1.synchronize()
-            zres[name] = e0.elapsed_time(e1) / reps_n * 1e3
+        for pc in ("zline", "zgroup"):
+            for name, x, y, reps_n in (("f32", x32, y32, 20), ("f64", x64, y64, 10)):
+                for _ in range(3):
+                    ctx.precond_apply(x, y, precond=pc)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps_n):
+                    ctx.precond_apply(x, y, precond=pc)
+                e1.record(stream)
+                e1.synchronize()
+                zres[pc + "_" + name] = e0.elapsed_time(e1) / reps_n * 1e3
         if rank == 0:
             print(json.dumps({"mode": "apply", "workload": args.workload, "ndof": ndof, "us": res,
                               "gdofs": {k: ndof / v / 1e3 for k, v in res.items()},

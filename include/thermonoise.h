@@ -57,7 +57,7 @@ enum { TN_BC_FREE = 0, TN_BC_FIXED = 1 };
 enum { TN_F64 = 0, TN_F32 = 1 };
 enum { TN_ISO = 0, TN_CUBIC = 1 };
 enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED_F32 = 1 };
-enum { TN_PC_JACOBI = 0, TN_PC_ZLINE = 1 };
+enum { TN_PC_JACOBI = 0, TN_PC_ZLINE = 1, TN_PC_ZGROUP = 2 };
 
 typedef struct tn_ctx tn_ctx;
 
@@ -143,15 +143,22 @@ tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
  * one column, all slabs, all nodes along zeta, three components), block
  * tridiagonal over the slabs, factorised by block Cholesky (FP64) and stored
  * in FP32 -- it captures the coupling across thin layers, whose elements
- * have aspect ratios up to ~1e4.  The first call after tn_build_mesh /
- * tn_set_materials builds the factors (2 * 3N^3 * n_slabs * 4 bytes per
- * column-node line).  precision TN_F64 / TN_F32 selects double / float
- * vectors r, z (caller-owned device buffers of tn_ndof() values, 16-byte
- * aligned, not overlapping). */
+ * have aspect ratios up to ~1e4.  TN_PC_ZGROUP (single mesh only): the
+ * same with the lines that meet at one point of the cross-section (matching
+ * nodes of the lateral faces of 2 to 4 neighbouring columns) taken together:
+ * the exact principal sub-matrix of A on each such group of lines, which adds
+ * the interior-penalty and flux coupling across the vertical element faces
+ * (Eqs. (numflux), (penalty)) that single lines leave out; TN_EINVAL if a
+ * node is shared by more than 4 columns.  The first call after
+ * tn_build_mesh / tn_set_materials builds the factors (FP64 set-up, about
+ * 1.5 (3 g N)^2 * n_slabs FP32 and FP64 entries per group of g lines).
+ * precision TN_F64 / TN_F32 selects double / float vectors r, z
+ * (caller-owned device buffers of tn_ndof() values, 16-byte aligned, not
+ * overlapping). */
 tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *r_dev, void *z_dev);
 
 /* Krylov solve of A u = b for the beam load (Sec. 2.3).
- * precond: TN_PC_JACOBI or TN_PC_ZLINE (see tn_precond_apply).
+ * precond: TN_PC_JACOBI, TN_PC_ZLINE or TN_PC_ZGROUP (see tn_precond_apply).
  * mode TN_SOLVE_F64: preconditioned CG in FP64, restarted from the current
  * iterate (true residual) if the recursive residual drifted.
  * mode TN_SOLVE_MIXED_F32: flexible CG in FP64 (residual, update and a window

@@ -112,14 +112,45 @@ struct tn_ctx {
   double *zpart = nullptr;
   int *zstatus = nullptr;
   bool zready = false;
+  // grouped-line preconditioner (same validity)
+  ZGroupPlan gplan;
+  ZGroupDev zgd;
+  int4 *d_glines = nullptr;
+  long long *d_gfac_off = nullptr;
+  float *gfac = nullptr;
+  double *gfac64 = nullptr;
+  double *gpart = nullptr;
+  int *gstatus = nullptr;
+  bool gready = false;
 };
 
-static void free_precond(tn_ctx *c) {
+static void free_zline(tn_ctx *c) {
   dfree(c->zfac);
   dfree(c->zfac64);
   dfree(c->zpart);
   dfree(c->zstatus);
   c->zready = false;
+}
+
+static void free_zgroup(tn_ctx *c) {
+  dfree(c->d_glines);
+  dfree(c->d_gfac_off);
+  dfree(c->gfac);
+  dfree(c->gfac64);
+  dfree(c->gpart);
+  dfree(c->gstatus);
+  for (int g = 0; g < 3; ++g) {
+    if (c->zgd.side[g]) cudaStreamDestroy(c->zgd.side[g]);
+    if (c->zgd.join[g]) cudaEventDestroy(c->zgd.join[g]);
+  }
+  if (c->zgd.fork) cudaEventDestroy(c->zgd.fork);
+  c->zgd = ZGroupDev();
+  c->gready = false;
+}
+
+static void free_precond(tn_ctx *c) {
+  free_zline(c);
+  free_zgroup(c);
 }
 
 static OpSys make_sys(const tn_ctx *c);
@@ -222,7 +253,7 @@ static tn_status ensure_fcg(tn_ctx *c, int m) {
 // builds the z-line factors on stream st (temporary FP64 blocks freed after)
 static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   if (c->zready) return TN_OK;
-  free_precond(c);
+  free_zline(c);
   size_t bb = 0, fb = 0;
   int nparts = 0;
   if (is_batch(c)) {
@@ -266,6 +297,70 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   if (status) return fail(TN_EBREAKDOWN, "z-line block not positive definite");
   c->zready = true;
   return TN_OK;
+}
+
+// builds the grouped-line factors (single mesh) on stream st; the FP64
+// set-up blocks and scratch are freed after
+static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
+  if (c->gready) return TN_OK;
+  if (is_batch(c)) return fail(TN_EINVAL, "TN_PC_ZGROUP needs a single mesh");
+  free_zgroup(c);
+  char msg[160];
+  if (!tn_zgroup_plan(c->hm, &c->gplan, msg, sizeof(msg))) return fail(TN_EINVAL, "%s", msg);
+  const ZGroupPlan &p = c->gplan;
+  const size_t bb = tn_zline_block_bytes(c->dm), xb = tn_zgroup_cross_bytes(c->dm),
+               wb = tn_zgroup_work_bytes(c->dm, p), fb = (size_t)p.nfac * sizeof(float);
+  double *blk = nullptr, *xblk = nullptr, *work = nullptr;
+  cudaError_t e = cudaMalloc((void **)&blk, bb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&xblk, xb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&work, wb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->gfac, fb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->gfac64, 2 * fb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->gpart, sizeof(double) * 2 * p.ngroups);  // r.z, r.r
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->gstatus, 2 * sizeof(int));  // factor status, solve timeout
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_glines, sizeof(int4) * p.ngroups);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gfac_off, sizeof(long long) * p.ngroups);
+  if (e != cudaSuccess) {
+    dfree(blk); dfree(xblk); dfree(work);
+    free_zgroup(c);
+    cudaGetLastError();
+    return fail(TN_ENOMEM, "grouped-line preconditioner needs %.2f GB: %s", (bb + xb + wb + 3 * fb) / 1e9,
+                cudaGetErrorString(e));
+  }
+  ZGroupDev &g = c->zgd;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&g.side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
+  g.lines = c->d_glines;
+  g.fac_off = c->d_gfac_off;
+  g.ngroups = p.ngroups;
+  for (int k = 0; k <= 4; ++k) { g.cls_start[k] = p.cls_start[k]; g.cls_n[k] = p.cls_n[k]; }
+  int status = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_glines, p.lines.data(), sizeof(int4) * p.ngroups,
+                                            cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_gfac_off, p.fac_off.data(), sizeof(long long) * p.ngroups,
+                                            cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->gstatus, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess)
+    e = tn_zgroup_setup(c->dm, p, c->d_glines, c->d_gfac_off, blk, xblk, work, c->gfac, c->gfac64, c->gstatus, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->gstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(blk); dfree(xblk); dfree(work);
+  if (e != cudaSuccess) { free_zgroup(c); return cuda_fail(e, "grouped-line set-up"); }
+  if (status) { free_zgroup(c); return fail(TN_EBREAKDOWN, "grouped-line block not positive definite"); }
+  c->gready = true;
+  return TN_OK;
+}
+
+// the operator system with the grouped-line solve in place of the single lines
+static OpSys with_groups(OpSys s, const tn_ctx *c) {
+  s.grouped = true;
+  s.zg = c->zgd;
+  s.n_rz_parts = c->zgd.ngroups;
+  s.zerr = c->gstatus + 1;
+  return s;
 }
 
 // per-layer energies of u (all mirrors of a batch, concatenated) into host out
@@ -807,7 +902,8 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (!o) return fail(TN_EINVAL, "opts is null");
   if ((st = check_buf(c, u, 8, "u"))) return st;
   if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
-  if (o->precond != TN_PC_JACOBI && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "unknown preconditioner");
+  if (o->precond != TN_PC_JACOBI && o->precond != TN_PC_ZLINE && o->precond != TN_PC_ZGROUP)
+    return fail(TN_EINVAL, "unknown preconditioner");
   if (is_batch(c) && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "a batch is solved with TN_PC_ZLINE");
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
   if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
@@ -829,13 +925,22 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (!is_batch(c)) CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
   double bb = 0.0;
   CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
-  const bool zl = o->precond == TN_PC_ZLINE;
-  if (zl) {
+  const bool zg = o->precond == TN_PC_ZGROUP;
+  const bool zl = o->precond == TN_PC_ZLINE || zg;  // a line-type solve (single or grouped lines)
+  if (zg) {
+    tn_status zs = ensure_zgroup(c, s);
+    if (zs != TN_OK) return zs;
+    CU_TRY(cudaMemsetAsync(c->gstatus + 1, 0, sizeof(int), s), "reset");
+  } else if (zl) {
     tn_status zs = ensure_zline(c, s);
     if (zs != TN_OK) return zs;
     CU_TRY(cudaMemsetAsync(c->zstatus + 1, 0, sizeof(int), s), "reset");
   }
-  const OpSys sys = make_sys(c);
+  const OpSys sys = zg ? with_groups(make_sys(c), c) : make_sys(c);
+  float *const lfac = zg ? c->gfac : c->zfac;
+  double *const lfac64 = zg ? c->gfac64 : c->zfac64;
+  double *const lpart = zg ? c->gpart : c->zpart;
+  int *const lstatus = zg ? c->gstatus : c->zstatus;
   tn_solve_report r{};
   tn_status result = TN_OK;
   if (bb == 0.0) {
@@ -843,7 +948,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   } else if (o->mode == TN_SOLVE_F64) {
     if (!is_batch(c)) CU_TRY(tn::pcg_setup_dinv(n, c->diag64, c->dinv64, TN_F64, s), "dinv");
     PcgVectors v{u, c->r64, c->z64, c->p64, c->q64, c->b64, c->dinv64};
-    if (zl) { v.zfac = c->zfac64; v.part_rz = c->zpart; }
+    if (zl) { v.zfac = lfac64; v.part_rz = lpart; }
     // FP64 PCG; restarted from the current iterate (true residual) if the
     // recursively updated residual drifted away from b - A x
     bool x0_zero = o->use_x0 == 0;
@@ -921,7 +1026,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       const double rn = std::sqrt(rr);
       CU_TRY(tn::cast_scaled(n, c->r64, 1.0 / rn, c->b32, c->d32, s), "cast");
       PcgVectors v{c->d32, c->r32, c->z32, c->p32, c->q32, c->b32, c->dinv32};
-      if (zl) { v.zfac = c->zfac; v.part_rz = c->zpart; }
+      if (zl) { v.zfac = lfac; v.part_rz = lpart; }
       int applies = 0;
       CU_TRY(tn::pcg_f32(sys, n, v, true, o->inner_rtol, kin, kin, c->scal, c->scal_host, c->part_elem,
                          c->part_red, s, &applies), "pcg f32");
@@ -968,7 +1073,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
                     r.rel_residual, o->rtol, r.inner_iters);
   }
   int zerr = 0;
-  if (zl) CU_TRY(cudaMemcpyAsync(&zerr, c->zstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+  if (zl) CU_TRY(cudaMemcpyAsync(&zerr, lstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   CU_TRY(cudaEventRecord(c->ev_out, s), "event");
   CU_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
   CU_TRY(cudaStreamSynchronize(s), "sync");
@@ -984,7 +1089,8 @@ tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r,
   tn_status st = need_ready(c, false);
   if (st) return st;
   if (precision != TN_F64 && precision != TN_F32) return fail(TN_EINVAL, "precision must be TN_F64 or TN_F32");
-  if (precond != TN_PC_JACOBI && precond != TN_PC_ZLINE) return fail(TN_EINVAL, "unknown preconditioner");
+  if (precond != TN_PC_JACOBI && precond != TN_PC_ZLINE && precond != TN_PC_ZGROUP)
+    return fail(TN_EINVAL, "unknown preconditioner");
   const size_t es = precision == TN_F64 ? 8 : 4;
   if ((st = check_buf(c, r, es, "r"))) return st;
   if ((st = check_buf(c, z, es, "z"))) return st;
@@ -992,6 +1098,14 @@ tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r,
   if (a < b + c->ndof * es && b < a + c->ndof * es) return fail(TN_EINVAL, "r and z overlap");
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   if ((st = ensure_ws(c))) return st;
+  if (precond == TN_PC_ZGROUP) {
+    if ((st = ensure_zgroup(c, c->stream))) return st;
+    CU_TRY(with_groups(make_sys(c), c)
+               .zsolve(precision, precision == TN_F64 ? (const void *)c->gfac64 : (const void *)c->gfac,
+                       const_cast<void *>(r), nullptr, z, nullptr, c->gpart, nullptr, c->stream),
+           "grouped-line solve");
+    return TN_OK;
+  }
   if (precond == TN_PC_ZLINE) {
     if ((st = ensure_zline(c, c->stream))) return st;
     CU_TRY(make_sys(c).zsolve(precision, precision == TN_F64 ? (const void *)c->zfac64 : (const void *)c->zfac,

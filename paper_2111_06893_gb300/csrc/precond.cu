@@ -15,6 +15,7 @@
 // one warp per line, the 3N unknowns of a slab on the lanes, forward and
 // backward block substitution.
 #include <cstdio>
+#include <vector>
 
 #include "tn_internal.h"
 #include "tn_precond.h"
@@ -579,6 +580,373 @@ zline_solve_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restr
   block_partial2((double)rz, (double)rr, part_rz, part_rr);
 }
 
+// ---------------------------------------------------------------- line groups
+// The lines through the matching nodes of two columns that share a lateral
+// face are coupled by that face's interior-penalty and flux terms (Eqs.
+// (numflux), (penalty)), which the single-line blocks leave out; with the
+// penalty ~ C (p + 1)^2 / h these are the stiffest couplings left.  A group
+// is a set of lines joined by such face matches (1 to 4 lines: a node inside
+// a column face, on a column edge or at a corner where up to four columns
+// meet); its block is the exact principal sub-matrix of A on all its lines,
+// again block tridiagonal over the slabs, with 3 g N unknowns per slab and
+// the cross-line face terms in the diagonal blocks.
+
+// Cross-line block of element e = (s, c), lateral face f and face position t:
+// rows = the line through the face node (this element), columns = the line
+// through the matching node of the neighbour column (same slab):
+//   -1/2 V^T W Tr_ext + 1/2 Tr^T W V_ext - V^T W Pen V_ext
+// restricted to the two lines (the neighbour's traction and this element's
+// test traction reduce to the zeta derivative and the diagonal xi / eta
+// derivative entries on a line).  Zero where f has no neighbour.
+template <int N>
+__global__ void zgroup_cross_kernel(const DevMesh m, double *__restrict__ xblk) {
+  constexpr int M = 3 * N, N2 = N * N;
+  const int e = blockIdx.x, t = threadIdx.x % N, f = threadIdx.x / N;
+  if (f >= 4) return;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  double *X = xblk + (((size_t)e * 4 + f) * N + t) * M * M;
+  for (int q = 0; q < M * M; ++q) X[q] = 0.0;
+  const int nbc = m.colnb[4 * c + f];
+  if (nbc < 0) return;
+  const int d = f >> 1, sd = f & 1, end = sd ? N - 1 : 0;
+  const int i = d == 0 ? end : t, j = d == 0 ? t : end;
+  const int code = m.colnbf[4 * c + f];
+  const int f2 = code & 3, d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+  const int a2 = (code >> 2) ? N - 1 - t : t;
+  const int i2 = d2 == 0 ? end2 : a2, j2 = d2 == 0 ? a2 : end2;
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const double *cg2 = m.colgeo + (size_t)nbc * CG_NF * N2;
+  const int q1 = j * N + i, q2 = j2 * N + i2;
+  const double ixx = cg[CG_IXX * N2 + q1], ixy = cg[CG_IXY * N2 + q1];
+  const double iex = cg[CG_IEX * N2 + q1], iey = cg[CG_IEY * N2 + q1], det2 = cg[CG_DET * N2 + q1];
+  const double jxx = cg2[CG_IXX * N2 + q2], jxy = cg2[CG_IXY * N2 + q2];
+  const double jex = cg2[CG_IEX * N2 + q2], jey = cg2[CG_IEY * N2 + q2];
+  const double *sg = m.slabgeo + (size_t)s * SG_NF * N;
+  double dz[N];
+  for (int k = 0; k < N; ++k) dz[k] = sg[SG_DZ * N + k];
+  const int L = m.slab_layer[s];  // both sides lie in slab s: one material
+  const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
+  const double rx = d == 0 ? ixx : iex, ry = d == 0 ? ixy : iey;
+  const double mag = sqrt(rx * rx + ry * ry);
+  const double n[3] = {(sd ? 1.0 : -1.0) * rx / mag, (sd ? 1.0 : -1.0) * ry / mag, 0.0};
+  const double sx = d2 == 0 ? jxx : jex, sy = d2 == 0 ? jxy : jey;
+  const double h = 2.0 / mag, h2 = 2.0 / sqrt(sx * sx + sy * sy);
+  const double sig = (double)((m.p + 1) * (m.p + 1)) * m.penC / (h < h2 ? h : h2);
+  const double Dii = LD(i, i), Djj = LD(j, j), Dii2 = LD(i2, i2), Djj2 = LD(j2, j2);
+  const double wt = d == 0 ? LW(j) : LW(i);
+  for (int k = 0; k < N; ++k) {
+    const double Wk = wt * LW(k) * det2 * dz[k] * mag;
+    for (int k2 = 0; k2 < N; ++k2) {
+      const double Wk2 = wt * LW(k2) * det2 * dz[k2] * mag;
+      // neighbour basis (i2, j2, k2) at its node (i2, j2, k); own basis (i, j, k) at (i, j, k2)
+      const double l2[3] = {k2 == k ? Dii2 : 0.0, k2 == k ? Djj2 : 0.0, LD(k, k2)};
+      const double l1[3] = {k == k2 ? Dii : 0.0, k == k2 ? Djj : 0.0, LD(k2, k)};
+      double g2[3], g1[3];
+      phys(l2, jxx, jxy, jex, jey, dz[k], g2);
+      phys(l1, ixx, ixy, iex, iey, dz[k2], g1);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double v = -0.5 * Wk * Qab(a, b, n, g2, c11, c12, c44) + 0.5 * Wk2 * Qab(b, a, n, g1, c11, c12, c44);
+          if (k == k2) v -= Wk * sig * Qab(a, b, n, n, c11, c12, c44);
+          X[(a * N + k) * M + b * N + k2] = v;
+        }
+    }
+  }
+}
+
+// block Cholesky along the slabs of one group (one CTA; FP64 working
+// matrices G, Linv, Z of (3 g N)^2 entries each in `work`), then FP32 and
+// FP64 records [Linv_s packed | Z_s] as for single lines
+template <int N>
+__global__ void __launch_bounds__(128)
+zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
+                     int gbase, int g, const double *__restrict__ blk, const double *__restrict__ xblk,
+                     double *__restrict__ work, float *__restrict__ fac, double *__restrict__ fac64,
+                     int *__restrict__ status) {
+  constexpr int M = 3 * N, N2 = N * N;
+  const int grp = gbase + blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int MG = g * M, S = m.nslab;
+  const int LP = zlp(MG), LDZ = zld(MG), RS = zrec(MG);
+  double *Gm = work + (size_t)blockIdx.x * 3 * MG * MG, *Li = Gm + MG * MG, *Z = Li + MG * MG;
+  __shared__ int lid[4], xof[4][4];
+  if (tid < 4) {
+    const int4 L4 = glines[grp];
+    lid[tid] = tid == 0 ? L4.x : (tid == 1 ? L4.y : (tid == 2 ? L4.z : L4.w));
+  }
+  __syncthreads();
+  if (tid < 16) {  // which face block couples line t1 (rows) to line t2 (columns)
+    const int t1 = tid >> 2, t2 = tid & 3;
+    int x = -1;
+    if (t1 < g && t2 < g && t1 != t2) {
+      const int c1 = lid[t1] / N2, qq = lid[t1] - c1 * N2, i1 = qq % N, j1 = qq / N;
+      for (int f = 0; f < 4; ++f) {
+        const int nbc = m.colnb[4 * c1 + f];
+        const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+        if (nbc < 0 || (d == 0 ? i1 : j1) != end) continue;
+        const int tp = d == 0 ? j1 : i1;
+        const int code = m.colnbf[4 * c1 + f], f2 = code & 3, d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+        const int a2 = (code >> 2) ? N - 1 - tp : tp;
+        const int i2 = d2 == 0 ? end2 : a2, j2 = d2 == 0 ? a2 : end2;
+        if (nbc * N2 + j2 * N + i2 == lid[t2]) x = f * N + tp;
+      }
+    }
+    xof[t1][t2] = x;
+  }
+  __syncthreads();
+  const long long rec0 = gfac[grp];
+  for (int s = 0; s < S; ++s) {
+    // diagonal block of slab s (line blocks, cross-line face blocks) minus Z_s^T Z_s
+    for (int q = tid; q < MG * MG; q += nth) {
+      const int r = q / MG, cc = q - r * MG, t1 = r / M, t2 = cc / M, rr = r - t1 * M, c2 = cc - t2 * M;
+      double v = 0.0;
+      if (t1 == t2) {
+        v = blk[(((size_t)lid[t1] * S + s) * 2 + 0) * M * M + rr * M + c2];
+      } else if (xof[t1][t2] >= 0) {
+        const size_t e = (size_t)s * m.ncol + lid[t1] / N2;
+        v = xblk[(e * 4 * N + xof[t1][t2]) * M * M + rr * M + c2];
+      }
+      if (s > 0)
+        for (int p = 0; p < MG; ++p) v -= Z[p * MG + r] * Z[p * MG + cc];
+      Gm[q] = v;
+    }
+    __syncthreads();
+    // Cholesky, lower triangle in place
+    for (int col = 0; col < MG; ++col) {
+      if (tid == 0) {
+        double dv = Gm[col * MG + col];
+        if (!(dv > 0.0)) {
+          atomicExch(status, 1);
+          dv = 1e-300;
+        }
+        Gm[col * MG + col] = sqrt(dv);
+      }
+      __syncthreads();
+      const double piv = Gm[col * MG + col];
+      for (int r = col + 1 + tid; r < MG; r += nth) Gm[r * MG + col] /= piv;
+      __syncthreads();
+      const int w = MG - col - 1;
+      for (int q = tid; q < w * w; q += nth) {
+        const int r = col + 1 + q / w, c2 = col + 1 + q % w;
+        if (c2 <= r) Gm[r * MG + c2] -= Gm[r * MG + col] * Gm[c2 * MG + col];
+      }
+      __syncthreads();
+    }
+    // Linv = L^{-1}, one column per thread (forward substitution on the
+    // identity); its upper triangle is zero (read by Z = Linv O below)
+    for (int cc = tid; cc < MG; cc += nth) {
+      for (int r = 0; r < cc; ++r) Li[r * MG + cc] = 0.0;
+      for (int r = cc; r < MG; ++r) {
+        double acc = r == cc ? 1.0 : 0.0;
+        for (int p = cc; p < r; ++p) acc -= Gm[r * MG + p] * Li[p * MG + cc];
+        Li[r * MG + cc] = acc / Gm[r * MG + r];
+      }
+    }
+    __syncthreads();
+    float *Lf = fac + rec0 + (long long)s * RS;
+    double *Ld = fac64 + rec0 + (long long)s * RS;
+    for (int q = tid; q < MG * MG; q += nth) {
+      const int r = q / MG, cc = q - r * MG;
+      if (r >= cc) {
+        const int pi = zcol(MG, cc) + r - cc;
+        Ld[pi] = Li[q];
+        Lf[pi] = (float)Li[q];
+      }
+    }
+    for (int q = MG * (MG + 1) / 2 + tid; q < LP; q += nth) { Lf[q] = 0.0f; Ld[q] = 0.0; }
+    for (int q = tid; q < RS - LP; q += nth) {
+      const int r = q / LDZ, cc = q - r * LDZ;
+      const double v = (s > 0 && r < MG && cc < MG) ? Z[r * MG + cc] : 0.0;
+      Lf[LP + q] = (float)v;
+      Ld[LP + q] = v;
+    }
+    __syncthreads();
+    if (s + 1 < S) {  // Z_{s+1} = Linv_s O_s, O_s block diagonal over the lines
+      for (int q = tid; q < MG * MG; q += nth) {
+        const int r = q / MG, cc = q - r * MG, t2 = cc / M, c2 = cc - t2 * M;
+        const double *O = blk + (((size_t)lid[t2] * S + s) * 2 + 1) * M * M;
+        double acc = 0.0;
+        for (int p = 0; p < M; ++p) acc += Li[r * MG + t2 * M + p] * O[p * M + c2];
+        Z[q] = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int N, int G>
+__host__ __device__ constexpr int zg_threads() { return 32 * ((G * 3 * N + 31) / 32); }
+template <int N, int G>
+__host__ __device__ constexpr int zg_part() {
+  return zlp(G * 3 * N) > zzp(G * 3 * N) ? zlp(G * 3 * N) : zzp(G * 3 * N);
+}
+// shared memory: two part buffers, two broadcast vectors, two mbarriers
+template <int N, int G, typename T>
+constexpr size_t zg_smem() { return (2 * (size_t)zg_part<N, G>() + 2 * zg_threads<N, G>()) * sizeof(T) + 16; }
+
+// z = A_GG^{-1} r on the groups of g = G lines [gbase, gbase + gridDim.x):
+// one group per CTA, one row (unknown of a slab) per thread.  The factor
+// parts are streamed through two shared buffers in the order they are used
+// (forward: L_0, Z_1, L_1, ...; backward: L_{S-1}, Z_{S-1}, L_{S-2}, ...), one
+// bulk copy each, the next in flight while the current one is used.  UPD,
+// partial sums and the timeout flag as for single lines.
+template <int N, int G, typename T, bool UPD>
+__global__ void __launch_bounds__(zg_threads<N, G>())
+zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
+                    int gbase, const T *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
+                    T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
+                    double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
+  if (done && *done) return;
+  constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = zg_threads<N, G>();
+  constexpr int LP = zlp(MG), LDZ = zld(MG), RS = zrec(MG), PB = zg_part<N, G>();
+  extern __shared__ __align__(16) unsigned char zsm[];
+  T *const buf0 = reinterpret_cast<T *>(zsm);
+  T *const vb = buf0 + 2 * PB;
+  T *const vx = vb + NT;
+  unsigned long long *const bar = reinterpret_cast<unsigned long long *>(vx + NT);
+  const int tid = threadIdx.x, grp = gbase + blockIdx.x;
+  const bool act = tid < MG;
+  const int t = act ? tid : 0;
+  const int4 L4 = glines[grp];
+  const int li = t / M, rem = t - li * M, a = rem / N, k = rem - a * N;
+  const int lid = li == 0 ? L4.x : (li == 1 ? L4.y : (li == 2 ? L4.z : L4.w));
+  const int c = lid / N2, qn = lid - c * N2;
+  const size_t off = (size_t)k * N2 + qn;
+  const size_t ncol = m.ncol;
+  const int S = m.nslab;
+  auto gidx = [&](int s) { return ((size_t)(s * ncol + c) * 3 + a) * n + off; };
+  const T *base = fac + gfac[grp];
+  const T al = UPD ? (T)*alpha : T(0);
+  const int total = 4 * S - 2;
+  unsigned ph = 0u, pend = 0u;
+  auto issue = [&](int u) {
+    const int b = u & 1;
+    if (tid == 0) {
+      int s;
+      bool isZ;
+      if (u < 2 * S - 1) {
+        s = (u + 1) >> 1;
+        isZ = (u & 1) != 0;
+      } else {
+        const int v = u - (2 * S - 1);  // L_{S-1}, Z_{S-1}, L_{S-2}, Z_{S-2}, ...
+        s = S - 1 - (v >> 1);
+        isZ = (v & 1) != 0;
+      }
+      const int cnt = isZ ? RS - LP : LP;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect(bar + b, (unsigned)(cnt * sizeof(T)));
+      bulk_g2s(buf0 + b * PB, base + (size_t)s * RS + (isZ ? LP : 0), (unsigned)(cnt * sizeof(T)), bar + b);
+    }
+    pend |= 1u << b;
+  };
+  auto wait = [&](int u) {
+    const int b = u & 1;
+    const bool ok = mbar_wait(bar + b, (ph >> b) & 1u);
+    ph ^= 1u << b;
+    pend &= ~(1u << b);
+    return ok;
+  };
+  if (tid == 0) {
+    mbar_init(bar);
+    mbar_init(bar + 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  T rz = T(0), rr = T(0);
+  bool bad = false;
+  int u = 0;
+  issue(0);
+  // forward sweep
+  T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
+  T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
+  T ylast = T(0);
+  for (int s = 0; s < S; ++s) {
+    T rv = r0;
+    if (UPD) {
+      rv -= al * q0;
+      if (act) r[gidx(s)] = rv;
+    }
+    r0 = r1;
+    q0 = q1;
+    if (act && s + 2 < S) {
+      r1 = r[gidx(s + 2)];
+      if (UPD) q1 = q[gidx(s + 2)];
+    }
+    rr += rv * rv;
+    T bv = rv;
+    if (s > 0) {  // part Z_s
+      if (u + 1 < total) issue(u + 1);
+      if (__syncthreads_or(!wait(u))) { bad = true; break; }
+      const T *Zs = buf0 + (u & 1) * PB;
+      bv -= bcast_dot<MG, T>(vx, [&](int cc) { return Zs[cc * LDZ + t]; });
+      ++u;
+    }
+    vb[tid] = act ? bv : T(0);
+    __syncthreads();  // vb complete; the Z buffer and vx are free
+    if (u + 1 < total) issue(u + 1);  // part L_s
+    if (__syncthreads_or(!wait(u))) { bad = true; break; }
+    const T *Ls = buf0 + (u & 1) * PB;
+    T y = bcast_dot<MG, T>(vb, [&](int cc) { return cc <= t ? Ls[zcol(MG, cc) + t - cc] : T(0); });
+    if (!act) y = T(0);
+    rz += y * y;
+    if (act) z[gidx(s)] = y;
+    vx[tid] = y;
+    ylast = y;
+    ++u;
+    __syncthreads();  // vx complete; the L buffer is free
+  }
+  // backward sweep
+  if (!bad) {
+    T y0 = ylast;
+    T y1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
+    T y2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
+    const int pl = zcol(MG, t) - t;
+    for (int s = S - 1; s >= 0; --s) {
+      T yv = y0;
+      y0 = y1;
+      y1 = y2;
+      if (act && s >= 3) y2 = z[gidx(s - 3)];
+      if (s + 1 < S) {  // part Z_{s+1}
+        if (u + 1 < total) issue(u + 1);
+        if (__syncthreads_or(!wait(u))) { bad = true; break; }
+        const T *Zn = buf0 + (u & 1) * PB;
+        yv -= bcast_dot<MG, T>(vx, [&](int cc) { return Zn[t * LDZ + cc]; });
+        ++u;
+      }
+      vb[tid] = act ? yv : T(0);
+      __syncthreads();
+      if (u + 1 < total) issue(u + 1);  // part L_s
+      if (__syncthreads_or(!wait(u))) { bad = true; break; }
+      const T *Ls = buf0 + (u & 1) * PB;
+      T x = bcast_dot<MG, T>(vb, [&](int cc) { return cc >= t ? Ls[pl + cc] : T(0); });
+      if (!act) x = T(0);
+      if (act) z[gidx(s)] = x;
+      vx[tid] = x;
+      ++u;
+      __syncthreads();
+    }
+  }
+  if (bad) {  // a copy never landed: bounded waits for what is in flight, then report
+    if (pend & 1u) mbar_wait(bar, ph & 1u);
+    if (pend & 2u) mbar_wait(bar + 1, (ph >> 1) & 1u);
+    if (tid == 0 && err) atomicExch(err, 1);
+  }
+  __shared__ double red[2][4];
+  double vrz = (double)rz, vrr = (double)rr;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vrz += __shfl_xor_sync(0xffffffffu, vrz, o);
+    vrr += __shfl_xor_sync(0xffffffffu, vrr, o);
+  }
+  if ((tid & 31) == 0) { red[0][tid >> 5] = vrz; red[1][tid >> 5] = vrr; }
+  __syncthreads();
+  if (tid == 0) {
+    double srz = 0.0, srr = 0.0;
+    for (int w = 0; w < NT / 32; ++w) { srz += red[0][w]; srr += red[1][w]; }
+    if (part_rz) part_rz[grp] = srz;
+    if (part_rr) part_rr[grp] = srr;
+  }
+}
+
 template <int N>
 cudaError_t setup_n(const DevMesh &m, double *blk, float *fac, double *fac64, int *status, cudaStream_t st) {
   zline_blocks_kernel<N><<<m.E, ((N * N + 31) / 32) * 32, 0, st>>>(m, blk);
@@ -649,7 +1017,172 @@ cudaError_t solve_batch_n(int prec, const DevMesh *meshes, const int2 *work, int
                                              part_rz, part_rr, done, zerr, st);
 }
 
+template <int N>
+cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, const int4 *lines, const long long *fac_off,
+                           double *blk, double *xblk, double *work, float *fac, double *fac64, int *status,
+                           cudaStream_t st) {
+  zline_blocks_kernel<N><<<m.E, ((N * N + 31) / 32) * 32, 0, st>>>(m, blk);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  zgroup_cross_kernel<N><<<m.E, ((4 * N + 31) / 32) * 32, 0, st>>>(m, xblk);
+  err = cudaGetLastError();
+  for (int g = 1; g <= 4 && err == cudaSuccess; ++g) {
+    if (!p.cls_n[g]) continue;
+    zgroup_factor_kernel<N><<<p.cls_n[g], 128, 0, st>>>(m, lines, fac_off, p.cls_start[g], g, blk, xblk, work,
+                                                         fac, fac64, status);
+    err = cudaGetLastError();
+  }
+  return err;
+}
+
+template <int N, int G, typename T, bool UPD>
+cudaError_t zgroup_launch(const DevMesh &m, const ZGroupDev &gd, const void *fac, void *r, const void *q, void *z,
+                          const double *alpha, double *prz, double *prr, const int *done, int *zerr,
+                          cudaStream_t st) {
+  constexpr size_t sm = zg_smem<N, G, T>();
+  cudaError_t err = zline_smem_optin(zgroup_solve_kernel<N, G, T, UPD>, sm);
+  if (err != cudaSuccess) return err;
+  zgroup_solve_kernel<N, G, T, UPD><<<gd.cls_n[G], zg_threads<N, G>(), sm, st>>>(
+      m, gd.lines, gd.fac_off, gd.cls_start[G], (const T *)fac, (T *)r, (const T *)q, (T *)z, alpha, prz, prr,
+      done, zerr);
+  return cudaGetLastError();
+}
+
+template <int N, int G>
+cudaError_t zgroup_launch_g(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+                            const void *q, void *z, const double *alpha, double *prz, double *prr,
+                            const int *done, int *zerr, cudaStream_t st) {
+  if (prec == TN_F64)
+    return q ? zgroup_launch<N, G, double, true>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+             : zgroup_launch<N, G, double, false>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+  return q ? zgroup_launch<N, G, float, true>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+           : zgroup_launch<N, G, float, false>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+}
+
+// the group sizes run concurrently: size 1 on st, sizes 2..4 on side streams
+// forked from and joined back into st (also inside a stream capture)
+template <int N>
+cudaError_t zgroup_solve_n(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+                           const void *q, void *z, const double *alpha, double *prz, double *prr,
+                           const int *done, int *zerr, cudaStream_t st) {
+  cudaError_t err = cudaEventRecord(gd.fork, st);
+  for (int g = 2; g <= 4 && err == cudaSuccess; ++g) {
+    if (!gd.cls_n[g]) continue;
+    cudaStream_t sg = gd.side[g - 2];
+    err = cudaStreamWaitEvent(sg, gd.fork, 0);
+    if (err != cudaSuccess) break;
+    if (g == 2) err = zgroup_launch_g<N, 2>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
+    if (g == 3) err = zgroup_launch_g<N, 3>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
+    if (g == 4) err = zgroup_launch_g<N, 4>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
+    if (err == cudaSuccess) err = cudaEventRecord(gd.join[g - 2], sg);
+  }
+  if (err == cudaSuccess && gd.cls_n[1])
+    err = zgroup_launch_g<N, 1>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+  for (int g = 2; g <= 4 && err == cudaSuccess; ++g)
+    if (gd.cls_n[g]) err = cudaStreamWaitEvent(st, gd.join[g - 2], 0);
+  return err;
+}
+
 }  // namespace
+
+// union-find over face matches of the lines (col * N^2 + j * N + i)
+static int uf_find(std::vector<int> &p, int x) {
+  while (p[x] != x) {
+    p[x] = p[p[x]];
+    x = p[x];
+  }
+  return x;
+}
+
+bool tn_zgroup_plan(const tn::HostMesh &hm, ZGroupPlan *p, char *msg, int msglen) {
+  const int N = hm.N, N2 = N * N, nl = hm.ncol * N2;
+  std::vector<int> par(nl);
+  for (int x = 0; x < nl; ++x) par[x] = x;
+  for (int c = 0; c < hm.ncol; ++c)
+    for (int f = 0; f < 4; ++f) {
+      const int nbc = hm.colnb[4 * c + f];
+      if (nbc < 0) continue;
+      const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+      const int code = hm.colnbf[4 * c + f], f2 = code & 3, d2 = f2 >> 1, end2 = (f2 & 1) ? N - 1 : 0;
+      for (int t = 0; t < N; ++t) {
+        const int i = d == 0 ? end : t, j = d == 0 ? t : end;
+        const int a2 = (code >> 2) ? N - 1 - t : t;
+        const int i2 = d2 == 0 ? end2 : a2, j2 = d2 == 0 ? a2 : end2;
+        const int ra = uf_find(par, c * N2 + j * N + i), rb = uf_find(par, nbc * N2 + j2 * N + i2);
+        if (ra != rb) par[ra < rb ? rb : ra] = ra < rb ? ra : rb;
+      }
+    }
+  std::vector<std::vector<int>> comp(nl);
+  for (int x = 0; x < nl; ++x) comp[uf_find(par, x)].push_back(x);  // members ascending
+  p->lines.clear();
+  p->fac_off.clear();
+  p->nfac = 0;
+  p->ngroups = 0;
+  for (int g = 0; g <= 4; ++g) { p->cls_start[g] = 0; p->cls_n[g] = 0; }
+  for (int x = 0; x < nl; ++x)
+    if (comp[x].size() > 4) {
+      std::snprintf(msg, msglen, "a cross-section node is shared by %d columns (line groups hold at most 4)",
+                    (int)comp[x].size());
+      return false;
+    }
+  const int S = hm.nslab;
+  for (int g = 1; g <= 4; ++g) {
+    p->cls_start[g] = p->ngroups;
+    const long long rec = zrec(g * 3 * N);
+    for (int x = 0; x < nl; ++x) {
+      if ((int)comp[x].size() != g) continue;
+      int4 v = make_int4(-1, -1, -1, -1);
+      v.x = comp[x][0];
+      if (g > 1) v.y = comp[x][1];
+      if (g > 2) v.z = comp[x][2];
+      if (g > 3) v.w = comp[x][3];
+      p->lines.push_back(v);
+      p->fac_off.push_back(p->nfac);
+      p->nfac += (long long)S * rec;
+      ++p->cls_n[g];
+      ++p->ngroups;
+    }
+  }
+  return true;
+}
+
+size_t tn_zgroup_cross_bytes(const DevMesh &m) {
+  const size_t M = 3 * m.N;
+  return (size_t)m.E * 4 * m.N * M * M * sizeof(double);
+}
+
+size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p) {
+  size_t mx = 0;
+  for (int g = 1; g <= 4; ++g) {
+    const size_t MG = (size_t)g * 3 * m.N, b = (size_t)p.cls_n[g] * 3 * MG * MG * sizeof(double);
+    mx = b > mx ? b : mx;
+  }
+  return mx;
+}
+
+cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, const int4 *lines, const long long *fac_off,
+                            double *blk, double *xblk, double *work, float *fac, double *fac64, int *status,
+                            cudaStream_t st) {
+  switch (m.N) {
+#define TN_CASE(NN) \
+    case NN: return zgroup_setup_n<NN>(m, p, lines, fac_off, blk, xblk, work, fac, fac64, status, st);
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tn_zgroup_solve(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+                            const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
+                            const int *done, int *zerr, cudaStream_t st) {
+  switch (m.N) {
+#define TN_CASE(NN) \
+    case NN: return zgroup_solve_n<NN>(m, gd, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st);
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 size_t tn_zline_block_bytes(const DevMesh &m) {
   const size_t M = 3 * m.N;

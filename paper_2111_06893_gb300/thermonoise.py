@@ -20,8 +20,8 @@ TN_BC_FREE, TN_BC_FIXED = 0, 1
 TN_F64, TN_F32 = 0, 1
 TN_ISO, TN_CUBIC = 0, 1
 TN_SOLVE_F64, TN_SOLVE_MIXED_F32 = 0, 1
-TN_PC_JACOBI, TN_PC_ZLINE = 0, 1
-PRECONDS = {"jacobi": TN_PC_JACOBI, "zline": TN_PC_ZLINE}
+TN_PC_JACOBI, TN_PC_ZLINE, TN_PC_ZGROUP = 0, 1, 2
+PRECONDS = {"jacobi": TN_PC_JACOBI, "zline": TN_PC_ZLINE, "zgroup": TN_PC_ZGROUP}
 STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_ENOTCONV",
           -5: "TN_EBREAKDOWN", -6: "TN_ETIMEOUT", -7: "TN_ESTATE"}
 
