@@ -54,18 +54,6 @@ def fp32_apply_flops_per_dof(N):
     return per_elem / (3 * N ** 3)
 
 
-def zline_factor_bytes(d):
-    """FP32 bytes of the column-line factors of one mirror: per line (column
-    x cross-section node) and slab, the packed inverse diagonal factor
-    M (M + 1) / 2 and the coupling block M x (M | 1), each padded to 4 entries
-    (M = 3 N)."""
-    N = d["degree"] + 1
-    M = 3 * N
-    pad4 = lambda v: (v + 3) // 4 * 4
-    rec = pad4(M * (M + 1) // 2) + pad4(M * (M | 1))
-    return W.n_columns(d) * N * N * (len(d["slab_z"]) - 1) * rec * 4
-
-
 # DRAM bytes (read + write) of one z-line solve launch (no residual update),
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of
 # `bench.py --mode apply`; absent where no capture of the current kernel exists
@@ -210,9 +198,11 @@ def main():
     ap.add_argument("--energy-rtol", type=float, default=1e-10,
                     help="stop once every U_i changes by less than this between checks")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
-    ap.add_argument("--inner-max", type=int, default=300)
+    ap.add_argument("--inner-max", type=int, default=None,
+                    help="default: 100 with grouped lines, 300 with single lines")
     ap.add_argument("--fcg-window", type=int, default=16)
-    ap.add_argument("--precond", default="zline", choices=["zline", "zgroup", "jacobi"])
+    ap.add_argument("--precond", default=None, choices=["zline", "zgroup", "jacobi"],
+                    help="default: grouped lines for one mirror, single lines for a batch")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-U solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-reference", action="store_true",
@@ -386,21 +376,25 @@ def main():
     t32 = time_apply(x32, y32, 200)
     t64 = time_apply(x64, y64, 20)
 
-    # the dominant kernel of the step: the FP32 column-line solve
+    # the dominant kernel of the step: the FP32 preconditioner solve (column lines)
+    pc = args.precond or ("zline" if batched else "zgroup")
+    if pc == "jacobi":
+        pc = "zline"
+
     def time_zline(x, y, reps_n):
         for _ in range(5):
-            ctx.precond_apply(x, y, precond="zline")
+            ctx.precond_apply(x, y, precond=pc)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps_n):
-            ctx.precond_apply(x, y, precond="zline")
+            ctx.precond_apply(x, y, precond=pc)
         e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1) / reps_n / 1e3
 
     tz = time_zline(x32, y32, 100)
-    zbytes = sum(zline_factor_bytes(d) for d in descs) + 8 * ndof  # factors once, r in, z out
+    zbytes = ctx.precond_factor_bytes(pc) + 8 * ndof  # factors once, r in, z out
     flops = flops_dof * ndof
     sm_max = 2070.0
     peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
@@ -447,8 +441,11 @@ def main():
     clocks = clk.summary()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
-    zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
-               else f"zline_solve_kernel<{N},float,float,0>")
+    if pc == "zgroup":
+        zkernel = f"zgroup_solve_kernel<{N},G,float,0>, G = 1..4 on concurrent streams"
+    else:
+        zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
+                   else f"zline_solve_kernel<{N},float,float,0>")
     line = {
         "metric": "GDOF/s of DG elasticity apply", "value": value, "unit": "GDOF/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -459,8 +456,9 @@ def main():
                    "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
                    "step": "rhs+mixed solve+energies+psd",
                    "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
-                   "inner_max": args.inner_max, "fcg_window": args.fcg_window,
-                   "precond": args.precond, "l2": "flushed between steps (256 MB)",
+                   "inner_max": args.inner_max or (100 if pc == "zgroup" else 300),
+                   "fcg_window": args.fcg_window,
+                   "precond": pc, "l2": "flushed between steps (256 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_U_s": {"mixed": mixed_s, "fp64": t_fp64,
                         "mixed_energy_rel_err": err_mixed,

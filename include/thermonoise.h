@@ -157,6 +157,11 @@ tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
  * overlapping). */
 tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *r_dev, void *z_dev);
 
+/* Bytes of FP32 factors one FP32 application of `precond` reads (building
+ * the factors first if needed; TN_PC_JACOBI: the inverse diagonal), for
+ * bandwidth accounting.  *bytes: host. */
+tn_status tn_precond_factor_bytes(tn_ctx *ctx, int precond, long long *bytes);
+
 /* Krylov solve of A u = b for the beam load (Sec. 2.3).
  * precond: TN_PC_JACOBI, TN_PC_ZLINE or TN_PC_ZGROUP (see tn_precond_apply).
  * mode TN_SOLVE_F64: preconditioned CG in FP64, restarted from the current

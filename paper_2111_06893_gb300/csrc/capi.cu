@@ -1085,6 +1085,29 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   return result;
 }
 
+tn_status tn_precond_factor_bytes(tn_ctx *c, int precond, long long *bytes) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if (!bytes) return fail(TN_EINVAL, "bytes is null");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  if ((st = ensure_ws(c))) return st;
+  if (precond == TN_PC_ZGROUP) {
+    if ((st = ensure_zgroup(c, c->stream))) return st;
+    *bytes = c->gplan.nfac * (long long)sizeof(float);
+    return TN_OK;
+  }
+  if (precond == TN_PC_ZLINE) {
+    if ((st = ensure_zline(c, c->stream))) return st;
+    *bytes = is_batch(c) ? c->batch->nfac * (long long)sizeof(float) : (long long)tn_zline_factor_bytes(c->dm);
+    return TN_OK;
+  }
+  if (precond == TN_PC_JACOBI) {
+    *bytes = (long long)c->ndof * (long long)sizeof(float);
+    return TN_OK;
+  }
+  return fail(TN_EINVAL, "unknown preconditioner");
+}
+
 tn_status tn_precond_apply(tn_ctx *c, int precond, int precision, const void *r, void *z) {
   tn_status st = need_ready(c, false);
   if (st) return st;

@@ -818,23 +818,34 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
   const T al = UPD ? (T)*alpha : T(0);
   const int total = 4 * S - 2;
   unsigned ph = 0u, pend = 0u;
+  // part u of the stream: forward L_0, Z_1, L_1, Z_2, ..., L_{S-1}; backward
+  // L_{S-1}, Z_{S-1}, L_{S-2}, Z_{S-2}, ..., Z_1, L_0
+  auto part = [&](int u, int &cnt) {
+    int s;
+    bool isZ;
+    if (u < 2 * S - 1) {
+      s = (u + 1) >> 1;
+      isZ = (u & 1) != 0;
+    } else {
+      const int v = u - (2 * S - 1);
+      s = S - 1 - (v >> 1);
+      isZ = (v & 1) != 0;
+    }
+    cnt = isZ ? RS - LP : LP;
+    return base + (size_t)s * RS + (isZ ? LP : 0);
+  };
   auto issue = [&](int u) {
     const int b = u & 1;
     if (tid == 0) {
-      int s;
-      bool isZ;
-      if (u < 2 * S - 1) {
-        s = (u + 1) >> 1;
-        isZ = (u & 1) != 0;
-      } else {
-        const int v = u - (2 * S - 1);  // L_{S-1}, Z_{S-1}, L_{S-2}, Z_{S-2}, ...
-        s = S - 1 - (v >> 1);
-        isZ = (v & 1) != 0;
-      }
-      const int cnt = isZ ? RS - LP : LP;
+      int cnt;
+      const T *src = part(u, cnt);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_expect(bar + b, (unsigned)(cnt * sizeof(T)));
-      bulk_g2s(buf0 + b * PB, base + (size_t)s * RS + (isZ ? LP : 0), (unsigned)(cnt * sizeof(T)), bar + b);
+      bulk_g2s(buf0 + b * PB, src, (unsigned)(cnt * sizeof(T)), bar + b);
+      if (u + 1 < total) {  // the part after it goes to L2 now
+        const T *nx = part(u + 1, cnt);
+        bulk_prefetch_l2(nx, (unsigned)(cnt * sizeof(T)));
+      }
     }
     pend |= 1u << b;
   };

@@ -29,7 +29,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
-           "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc"]
+           "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes"]
 
 
 class MeshDesc(C.Structure):
@@ -97,6 +97,7 @@ def load():
         "tn_layer_energies": (C.c_int, [vp, vp, dp]),
         "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
+        "tn_precond_factor_bytes": (C.c_int, [vp, C.c_int, C.POINTER(C.c_longlong)]),
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
                                      C.POINTER(SolveReport)]),
         "tn_layer_energies_noalloc": (C.c_int, [vp, vp, dp]),
@@ -195,6 +196,7 @@ class Context:
         _check(load().tn_build_mesh(self._h, C.byref(d)))
         del keep
         self.desc = desc
+        self.descs = None
         return self
 
     def set_materials(self, mats):
@@ -285,10 +287,23 @@ class Context:
         o.use_x0 = 0
         return o
 
+    def _precond(self, precond):
+        """None: grouped lines for a single mirror, single lines for a batch."""
+        if precond is not None:
+            return precond
+        return "zline" if getattr(self, "descs", None) is not None else "zgroup"
+
+    def precond_factor_bytes(self, precond=None):
+        """FP32 factor bytes one FP32 application of the preconditioner reads."""
+        b = C.c_longlong(0)
+        _check(load().tn_precond_factor_bytes(self._h, PRECONDS[self._precond(precond)], C.byref(b)))
+        return int(b.value)
+
     def energy_grad(self, u, w, mode="f64", rtol=1e-12, inner_rtol=0.05, max_iter=200000, max_outer=60,
-                    check_every=25, precond="zline", raise_on_error=True):
+                    check_every=25, precond=None, raise_on_error=True):
         """Adjoint gradient of J = sum_i w_i U_i at the solution u: returns
         dJ/dslab_z (n_slabs + 1), dJ/dr0, dJ/d(c11, c12, c44) per layer."""
+        precond = self._precond(precond)
         self._check_tensor(u, self._torch.float64, "u")
         nl = len(self.desc["materials"])
         w = np.ascontiguousarray(w, dtype=np.float64)
@@ -319,8 +334,15 @@ class Context:
         return {"instances": out, "report": rep.as_dict()}
 
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
-              x0=None, check_every=25, out=None, raise_on_error=True, precond="zline",
-              energy_rtol=0.0, inner_max=300, fcg_window=16):
+              x0=None, check_every=25, out=None, raise_on_error=True, precond=None,
+              energy_rtol=0.0, inner_max=None, fcg_window=16):
+        """precond None: grouped lines for one mirror, single lines for a
+        batch.  inner_max None: 100 FP32 iterations per flexible-CG step with
+        grouped lines, 300 with single lines (measured best on the 2.0 M DOF
+        single-coating mirror)."""
+        precond = self._precond(precond)
+        if inner_max is None:
+            inner_max = 100 if precond == "zgroup" else 300
         o = SolveOpts()
         o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
         o.precond = PRECONDS[precond]
