@@ -54,10 +54,13 @@ def fp32_apply_flops_per_dof(N):
     return per_elem / (3 * N ** 3)
 
 
-# DRAM bytes (read + write) of one z-line solve launch (no residual update),
-# from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of
-# `bench.py --mode apply`; absent where no capture of the current kernel exists
-ZLINE_TRAFFIC = {}
+# DRAM bytes (read + write) of one preconditioner solve (no residual update),
+# summed over its launches, from `ncu --set full -k regex:zgroup_solve_kernel`
+# of `bench.py --mode apply --workload single_coating`; absent where no
+# capture of the current kernels exists
+ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, G = 1..4 on concurrent streams"):
+                 (342.959104 + 11.750400) + (3.683072 + 0.0) + (86.450432 + 3.121152) + (205.297664 + 7.234816)}
+ZLINE_TRAFFIC = {k: v * 1e6 for k, v in ZLINE_TRAFFIC.items()}
 
 
 def measured_peaks():
@@ -394,7 +397,9 @@ def main():
         return e0.elapsed_time(e1) / reps_n / 1e3
 
     tz = time_zline(x32, y32, 100)
-    zbytes = ctx.precond_factor_bytes(pc) + 8 * ndof  # factors once, r in, z out
+    # the forward and the backward sweep each read every factor record (the
+    # factors are far larger than L2), r in and z out
+    zbytes = 2 * ctx.precond_factor_bytes(pc) + 8 * ndof
     flops = flops_dof * ndof
     sm_max = 2070.0
     peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
