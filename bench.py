@@ -58,9 +58,7 @@ def fp32_apply_flops_per_dof(N):
 # summed over its launches, from `ncu --set full -k regex:zgroup_solve_kernel`
 # of `bench.py --mode apply --workload single_coating`; absent where no
 # capture of the current kernels exists
-ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, G = 1..4 on concurrent streams"):
-                 (342.959104 + 11.750400) + (3.683072 + 0.0) + (86.450432 + 3.121152) + (205.297664 + 7.234816)}
-ZLINE_TRAFFIC = {k: v * 1e6 for k, v in ZLINE_TRAFFIC.items()}
+ZLINE_TRAFFIC = {}
 
 
 def measured_peaks():

@@ -654,6 +654,17 @@ __global__ void zgroup_cross_kernel(const DevMesh m, double *__restrict__ xblk) 
   }
 }
 
+// Group record of slab s: [Linv_s packed by columns (zlp(MG)) | O_{s-1} in
+// factored form (8 MG)].  The coupling block O_{s-1} (rows: slab s - 1,
+// columns: slab s, block diagonal over the lines) is nonzero only in the
+// rows of the bottom-face nodes (k = 0) and the columns of the top-face
+// nodes (k2 = N - 1) of each line (Eqs. (numflux), (penalty) on the zeta
+// face), so O = E_0 X^T + Y E_{N-1}^T with per row t: X[t][a] = O[(a, 0), t]
+// and Y[t][b] = O[t, (b, N - 1)] (Y zero on k = 0 rows).  Row t stores
+// X[t][0..2], 0, Y[t][0..2], 0.  The solve applies Z_s = Linv_{s-1} O_{s-1}
+// through Linv and these factors instead of storing Z densely.
+__host__ __device__ constexpr int zg_rec(int MG) { return zlp(MG) + 8 * MG; }
+
 // block Cholesky along the slabs of one group (one CTA; FP64 working
 // matrices G, Linv, Z of (3 g N)^2 entries each in `work`), then FP32 and
 // FP64 records [Linv_s packed | Z_s] as for single lines
@@ -666,7 +677,7 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
   constexpr int M = 3 * N, N2 = N * N;
   const int grp = gbase + blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int MG = g * M, S = m.nslab;
-  const int LP = zlp(MG), LDZ = zld(MG), RS = zrec(MG);
+  const int LP = zlp(MG), RS = zg_rec(MG);
   double *Gm = work + (size_t)blockIdx.x * 3 * MG * MG, *Li = Gm + MG * MG, *Z = Li + MG * MG;
   __shared__ int lid[4], xof[4][4];
   if (tid < 4) {
@@ -753,9 +764,14 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
       }
     }
     for (int q = MG * (MG + 1) / 2 + tid; q < LP; q += nth) { Lf[q] = 0.0f; Ld[q] = 0.0; }
-    for (int q = tid; q < RS - LP; q += nth) {
-      const int r = q / LDZ, cc = q - r * LDZ;
-      const double v = (s > 0 && r < MG && cc < MG) ? Z[r * MG + cc] : 0.0;
+    for (int q = tid; q < 8 * MG; q += nth) {  // factors of O_{s-1}
+      const int t = q >> 3, j = q & 7, l = t / M, tl = t - l * M, tk = tl % N;
+      double v = 0.0;
+      if (s > 0 && (j & 3) < 3) {
+        const double *O = blk + (((size_t)lid[l] * S + (s - 1)) * 2 + 1) * M * M;
+        if (j < 4) v = O[(j * N) * M + tl];                        // X[t][a] = O[(a, 0), t]
+        else if (tk != 0) v = O[tl * M + (j - 4) * N + (N - 1)];  // Y[t][b] = O[t, (b, N - 1)]
+      }
       Lf[LP + q] = (float)v;
       Ld[LP + q] = v;
     }
@@ -775,20 +791,20 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
 
 template <int N, int G>
 __host__ __device__ constexpr int zg_threads() { return 32 * ((G * 3 * N + 31) / 32); }
-template <int N, int G>
-__host__ __device__ constexpr int zg_part() {
-  return zlp(G * 3 * N) > zzp(G * 3 * N) ? zlp(G * 3 * N) : zzp(G * 3 * N);
-}
-// shared memory: two part buffers, two broadcast vectors, two mbarriers
+// shared memory: two stage buffers of one record, five vectors of NT entries
+// (b, y, w / x, three reduction rows), two mbarriers
 template <int N, int G, typename T>
-constexpr size_t zg_smem() { return (2 * (size_t)zg_part<N, G>() + 2 * zg_threads<N, G>()) * sizeof(T) + 16; }
+constexpr size_t zg_smem() { return (2 * (size_t)zg_rec(G * 3 * N) + 6 * zg_threads<N, G>()) * sizeof(T) + 16; }
 
 // z = A_GG^{-1} r on the groups of g = G lines [gbase, gbase + gridDim.x):
-// one group per CTA, one row (unknown of a slab) per thread.  The factor
-// parts are streamed through two shared buffers in the order they are used
-// (forward: L_0, Z_1, L_1, ...; backward: L_{S-1}, Z_{S-1}, L_{S-2}, ...), one
-// bulk copy each, the next in flight while the current one is used.  UPD,
-// partial sums and the timeout flag as for single lines.
+// one group per CTA, one row (unknown of a slab) per thread.
+//   forward   y_s = Linv_s (r_s - O_{s-1}^T w_{s-1}),  w_s = Linv_s^T y_s
+//   backward  x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1})
+// (Z_s = Linv_{s-1} O_{s-1}); O in its factored form needs three sums over
+// each line's rows per step.  Forward stage s = record s; backward stage s =
+// Linv_s and the O factors of record s + 1; one stage in flight while the
+// other is used (bulk copies, mbarriers), the next stage's data sent to L2.
+// UPD, partial sums and the timeout flag as for single lines.
 template <int N, int G, typename T, bool UPD>
 __global__ void __launch_bounds__(zg_threads<N, G>())
 zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
@@ -797,17 +813,19 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
                     double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
   if (done && *done) return;
   constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = zg_threads<N, G>();
-  constexpr int LP = zlp(MG), LDZ = zld(MG), RS = zrec(MG), PB = zg_part<N, G>();
+  constexpr int LP = zlp(MG), RS = zg_rec(MG);
   extern __shared__ __align__(16) unsigned char zsm[];
   T *const buf0 = reinterpret_cast<T *>(zsm);
-  T *const vb = buf0 + 2 * PB;
-  T *const vx = vb + NT;
-  unsigned long long *const bar = reinterpret_cast<unsigned long long *>(vx + NT);
+  T *const vb = buf0 + 2 * RS;
+  T *const vy = vb + NT;
+  T *const vw = vy + NT;
+  T *const red = vw + NT;  // 3 x NT
+  unsigned long long *const bar = reinterpret_cast<unsigned long long *>(red + 3 * NT);
   const int tid = threadIdx.x, grp = gbase + blockIdx.x;
   const bool act = tid < MG;
   const int t = act ? tid : 0;
   const int4 L4 = glines[grp];
-  const int li = t / M, rem = t - li * M, a = rem / N, k = rem - a * N;
+  const int li = t / M, rem = t - li * M, a = rem / N, k = rem - a * N, lb = li * M;
   const int lid = li == 0 ? L4.x : (li == 1 ? L4.y : (li == 2 ? L4.z : L4.w));
   const int c = lid / N2, qn = lid - c * N2;
   const size_t off = (size_t)k * N2 + qn;
@@ -816,35 +834,37 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
   auto gidx = [&](int s) { return ((size_t)(s * ncol + c) * 3 + a) * n + off; };
   const T *base = fac + gfac[grp];
   const T al = UPD ? (T)*alpha : T(0);
-  const int total = 4 * S - 2;
+  const int total = 2 * S;
   unsigned ph = 0u, pend = 0u;
-  // part u of the stream: forward L_0, Z_1, L_1, Z_2, ..., L_{S-1}; backward
-  // L_{S-1}, Z_{S-1}, L_{S-2}, Z_{S-2}, ..., Z_1, L_0
-  auto part = [&](int u, int &cnt) {
-    int s;
-    bool isZ;
-    if (u < 2 * S - 1) {
-      s = (u + 1) >> 1;
-      isZ = (u & 1) != 0;
+  // stage u: forward u = s (record s); backward u = 2S - 1 - s (Linv_s, O factors of record s + 1)
+  auto stage_src = [&](int u, const T *&s0, int &n0, const T *&s1, int &n1) {
+    if (u < S) {
+      s0 = base + (size_t)u * RS;
+      n0 = RS;
+      s1 = nullptr;
+      n1 = 0;
     } else {
-      const int v = u - (2 * S - 1);
-      s = S - 1 - (v >> 1);
-      isZ = (v & 1) != 0;
+      const int s = 2 * S - 1 - u;
+      s0 = base + (size_t)s * RS;
+      n0 = LP;
+      s1 = base + (size_t)(s + 1) * RS + LP;
+      n1 = s + 1 < S ? RS - LP : 0;
     }
-    cnt = isZ ? RS - LP : LP;
-    return base + (size_t)s * RS + (isZ ? LP : 0);
   };
   auto issue = [&](int u) {
     const int b = u & 1;
     if (tid == 0) {
-      int cnt;
-      const T *src = part(u, cnt);
+      const T *s0, *s1;
+      int n0, n1;
+      stage_src(u, s0, n0, s1, n1);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_expect(bar + b, (unsigned)(cnt * sizeof(T)));
-      bulk_g2s(buf0 + b * PB, src, (unsigned)(cnt * sizeof(T)), bar + b);
-      if (u + 1 < total) {  // the part after it goes to L2 now
-        const T *nx = part(u + 1, cnt);
-        bulk_prefetch_l2(nx, (unsigned)(cnt * sizeof(T)));
+      mbar_expect(bar + b, (unsigned)((n0 + n1) * sizeof(T)));
+      bulk_g2s(buf0 + b * RS, s0, (unsigned)(n0 * sizeof(T)), bar + b);
+      if (n1) bulk_g2s(buf0 + b * RS + LP, s1, (unsigned)(n1 * sizeof(T)), bar + b);
+      if (u + 1 < total) {  // the stage after it goes to L2 now
+        stage_src(u + 1, s0, n0, s1, n1);
+        bulk_prefetch_l2(s0, (unsigned)(n0 * sizeof(T)));
+        if (n1) bulk_prefetch_l2(s1, (unsigned)(n1 * sizeof(T)));
       }
     }
     pend |= 1u << b;
@@ -861,16 +881,37 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
     mbar_init(bar + 1);
     mbar_init_fence();
   }
+  vw[tid] = T(0);
   __syncthreads();
   T rz = T(0), rr = T(0);
   bool bad = false;
-  int u = 0;
+  const int pl = zcol(MG, t) - t;
+  auto lower = [&](const T *Ls, const T *v) {  // (Linv v)_t
+    return bcast_dot<MG, T>(v, [&](int cc) { return cc <= t ? Ls[zcol(MG, cc) + t - cc] : T(0); });
+  };
+  auto upper = [&](const T *Ls, const T *v) {  // (Linv^T v)_t
+    return bcast_dot<MG, T>(v, [&](int cc) { return cc >= t ? Ls[pl + cc] : T(0); });
+  };
+  // sum over this thread's line of red[j][.]
+  auto line_sum = [&](int j) {
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int i = 0; i + 1 < M; i += 2) {
+      s0 += red[j * NT + lb + i];
+      s1 += red[j * NT + lb + i + 1];
+    }
+    if (M & 1) s0 += red[j * NT + lb + M - 1];
+    return s0 + s1;
+  };
   issue(0);
   // forward sweep
   T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
   T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
   T ylast = T(0);
   for (int s = 0; s < S; ++s) {
+    if (s + 1 < total) issue(s + 1);
+    if (__syncthreads_or(!wait(s))) { bad = true; break; }
+    const T *Ls = buf0 + (s & 1) * RS, *XY = Ls + LP + 8 * t;
     T rv = r0;
     if (UPD) {
       rv -= al * q0;
@@ -884,55 +925,61 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
     }
     rr += rv * rv;
     T bv = rv;
-    if (s > 0) {  // part Z_s
-      if (u + 1 < total) issue(u + 1);
-      if (__syncthreads_or(!wait(u))) { bad = true; break; }
-      const T *Zs = buf0 + (u & 1) * PB;
-      bv -= bcast_dot<MG, T>(vx, [&](int cc) { return Zs[cc * LDZ + t]; });
-      ++u;
+    if (s > 0) {  // bv -= (O_{s-1}^T w_{s-1})_t
+      const T wv = vw[tid];
+      red[0 * NT + tid] = act ? XY[4] * wv : T(0);
+      red[1 * NT + tid] = act ? XY[5] * wv : T(0);
+      red[2 * NT + tid] = act ? XY[6] * wv : T(0);
+      __syncthreads();
+      T o = XY[0] * vw[lb] + XY[1] * vw[lb + N] + XY[2] * vw[lb + 2 * N];
+      if (k == N - 1) o += line_sum(a);
+      bv -= o;
     }
     vb[tid] = act ? bv : T(0);
-    __syncthreads();  // vb complete; the Z buffer and vx are free
-    if (u + 1 < total) issue(u + 1);  // part L_s
-    if (__syncthreads_or(!wait(u))) { bad = true; break; }
-    const T *Ls = buf0 + (u & 1) * PB;
-    T y = bcast_dot<MG, T>(vb, [&](int cc) { return cc <= t ? Ls[zcol(MG, cc) + t - cc] : T(0); });
+    __syncthreads();
+    T y = lower(Ls, vb);
     if (!act) y = T(0);
     rz += y * y;
     if (act) z[gidx(s)] = y;
-    vx[tid] = y;
+    vy[tid] = y;
     ylast = y;
-    ++u;
-    __syncthreads();  // vx complete; the L buffer is free
+    __syncthreads();
+    const T w = upper(Ls, vy);
+    vw[tid] = act ? w : T(0);
+    __syncthreads();  // vw complete; stage s is free
   }
   // backward sweep
   if (!bad) {
     T y0 = ylast;
     T y1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
     T y2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
-    const int pl = zcol(MG, t) - t;
     for (int s = S - 1; s >= 0; --s) {
+      const int u = 2 * S - 1 - s;
+      if (u + 1 < total) issue(u + 1);
+      if (__syncthreads_or(!wait(u))) { bad = true; break; }
+      const T *Ls = buf0 + (u & 1) * RS, *XY = Ls + LP + 8 * t;
       T yv = y0;
       y0 = y1;
       y1 = y2;
       if (act && s >= 3) y2 = z[gidx(s - 3)];
-      if (s + 1 < S) {  // part Z_{s+1}
-        if (u + 1 < total) issue(u + 1);
-        if (__syncthreads_or(!wait(u))) { bad = true; break; }
-        const T *Zn = buf0 + (u & 1) * PB;
-        yv -= bcast_dot<MG, T>(vx, [&](int cc) { return Zn[t * LDZ + cc]; });
-        ++u;
+      if (s + 1 < S) {  // yv -= (Linv_s O_s x_{s+1})_t
+        const T xv = vw[tid];
+        red[0 * NT + tid] = act ? XY[0] * xv : T(0);
+        red[1 * NT + tid] = act ? XY[1] * xv : T(0);
+        red[2 * NT + tid] = act ? XY[2] * xv : T(0);
+        __syncthreads();
+        T v = XY[4] * vw[lb + N - 1] + XY[5] * vw[lb + 2 * N - 1] + XY[6] * vw[lb + 3 * N - 1];
+        if (k == 0) v += line_sum(a);
+        vb[tid] = act ? v : T(0);
+        __syncthreads();
+        yv -= lower(Ls, vb);
       }
-      vb[tid] = act ? yv : T(0);
+      vy[tid] = act ? yv : T(0);
       __syncthreads();
-      if (u + 1 < total) issue(u + 1);  // part L_s
-      if (__syncthreads_or(!wait(u))) { bad = true; break; }
-      const T *Ls = buf0 + (u & 1) * PB;
-      T x = bcast_dot<MG, T>(vb, [&](int cc) { return cc >= t ? Ls[pl + cc] : T(0); });
+      T x = upper(Ls, vy);
       if (!act) x = T(0);
       if (act) z[gidx(s)] = x;
-      vx[tid] = x;
-      ++u;
+      vw[tid] = x;
       __syncthreads();
     }
   }
@@ -941,18 +988,18 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
     if (pend & 2u) mbar_wait(bar + 1, (ph >> 1) & 1u);
     if (tid == 0 && err) atomicExch(err, 1);
   }
-  __shared__ double red[2][4];
+  __shared__ double rsum[2][4];
   double vrz = (double)rz, vrr = (double)rr;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     vrz += __shfl_xor_sync(0xffffffffu, vrz, o);
     vrr += __shfl_xor_sync(0xffffffffu, vrr, o);
   }
-  if ((tid & 31) == 0) { red[0][tid >> 5] = vrz; red[1][tid >> 5] = vrr; }
+  if ((tid & 31) == 0) { rsum[0][tid >> 5] = vrz; rsum[1][tid >> 5] = vrr; }
   __syncthreads();
   if (tid == 0) {
     double srz = 0.0, srr = 0.0;
-    for (int w = 0; w < NT / 32; ++w) { srz += red[0][w]; srr += red[1][w]; }
+    for (int w = 0; w < NT / 32; ++w) { srz += rsum[0][w]; srr += rsum[1][w]; }
     if (part_rz) part_rz[grp] = srz;
     if (part_rr) part_rr[grp] = srr;
   }
@@ -1139,7 +1186,7 @@ bool tn_zgroup_plan(const tn::HostMesh &hm, ZGroupPlan *p, char *msg, int msglen
   const int S = hm.nslab;
   for (int g = 1; g <= 4; ++g) {
     p->cls_start[g] = p->ngroups;
-    const long long rec = zrec(g * 3 * N);
+    const long long rec = zg_rec(g * 3 * N);
     for (int x = 0; x < nl; ++x) {
       if ((int)comp[x].size() != g) continue;
       int4 v = make_int4(-1, -1, -1, -1);
