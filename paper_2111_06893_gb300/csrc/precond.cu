@@ -1124,7 +1124,7 @@ cudaError_t zgroup_solve_n(const DevMesh &m, const ZGroupDev &gd, int prec, cons
                            const void *q, void *z, const double *alpha, double *prz, double *prr,
                            const int *done, int *zerr, cudaStream_t st) {
   cudaError_t err = cudaEventRecord(gd.fork, st);
-  for (int g = 2; g <= 4 && err == cudaSuccess; ++g) {
+  for (int g = 4; g >= 2 && err == cudaSuccess; --g) {  // the longest chains first
     if (!gd.cls_n[g]) continue;
     cudaStream_t sg = gd.side[g - 2];
     err = cudaStreamWaitEvent(sg, gd.fork, 0);
