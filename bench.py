@@ -58,7 +58,8 @@ def fp32_apply_flops_per_dof(N):
 # summed over its launches, from `ncu --set full -k regex:zgroup_solve_kernel`
 # of `bench.py --mode apply --workload single_coating`; absent where no
 # capture of the current kernels exists
-ZLINE_TRAFFIC = {}
+ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, one launch per (N, G) class on concurrent streams"):
+                 (43.241984 + 0.001536 + 2.476544 + 131.687168 + 4.2112 + 101.7792 + 3.5136) * 1e6}
 
 
 def measured_peaks():
@@ -203,7 +204,7 @@ def main():
                     help="default: 100 with grouped lines, 300 with single lines")
     ap.add_argument("--fcg-window", type=int, default=16)
     ap.add_argument("--precond", default=None, choices=["zline", "zgroup", "jacobi"],
-                    help="default: grouped lines for one mirror, single lines for a batch")
+                    help="default: grouped lines")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 time-to-U solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-reference", action="store_true",
@@ -378,7 +379,7 @@ def main():
     t64 = time_apply(x64, y64, 20)
 
     # the dominant kernel of the step: the FP32 preconditioner solve (column lines)
-    pc = args.precond or ("zline" if batched else "zgroup")
+    pc = args.precond or "zgroup"
     if pc == "jacobi":
         pc = "zline"
 
@@ -445,7 +446,8 @@ def main():
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
     if pc == "zgroup":
-        zkernel = f"zgroup_solve_kernel<{N},G,float,0>, G = 1..4 on concurrent streams"
+        zkernel = (f"zgroup_solve_kernel<{'N' if batched else N},G,float,0>, "
+                   "one launch per (N, G) class on concurrent streams")
     else:
         zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
                    else f"zline_solve_kernel<{N},float,float,0>")

@@ -143,7 +143,7 @@ tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
  * one column, all slabs, all nodes along zeta, three components), block
  * tridiagonal over the slabs, factorised by block Cholesky (FP64) and stored
  * in FP32 -- it captures the coupling across thin layers, whose elements
- * have aspect ratios up to ~1e4.  TN_PC_ZGROUP (single mesh only): the
+ * have aspect ratios up to ~1e4.  TN_PC_ZGROUP (one mesh or a batch): the
  * same with the lines that meet at one point of the cross-section (matching
  * nodes of the lateral faces of 2 to 4 neighbouring columns) taken together:
  * the exact principal sub-matrix of A on each such group of lines, which adds
@@ -246,7 +246,7 @@ tn_status tn_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const double *u
  *   - tn_apply_operator applies the block-diagonal operator of all mirrors:
  *     one launch per polynomial degree present, each CTA working on one
  *     element of one mirror;
- *   - tn_precond_apply (TN_PC_ZLINE only) and tn_solve solve all mirrors at
+ *   - tn_precond_apply (TN_PC_ZLINE, TN_PC_ZGROUP) and tn_solve solve all mirrors at
  *     once (one Krylov iteration serves every mirror; the energy test covers
  *     every layer of every mirror);
  *   - tn_layer_energies returns the energies of all layers of all mirrors.

@@ -117,6 +117,7 @@ struct tn_ctx {
   ZGroupDev zgd;
   int4 *d_glines = nullptr;
   long long *d_gfac_off = nullptr;
+  int *d_ginst = nullptr;
   float *gfac = nullptr;
   double *gfac64 = nullptr;
   double *gpart = nullptr;
@@ -135,11 +136,12 @@ static void free_zline(tn_ctx *c) {
 static void free_zgroup(tn_ctx *c) {
   dfree(c->d_glines);
   dfree(c->d_gfac_off);
+  dfree(c->d_ginst);
   dfree(c->gfac);
   dfree(c->gfac64);
   dfree(c->gpart);
   dfree(c->gstatus);
-  for (int g = 0; g < 3; ++g) {
+  for (int g = 0; g < kZgSide; ++g) {
     if (c->zgd.side[g]) cudaStreamDestroy(c->zgd.side[g]);
     if (c->zgd.join[g]) cudaEventDestroy(c->zgd.join[g]);
   }
@@ -299,17 +301,30 @@ static tn_status ensure_zline(tn_ctx *c, cudaStream_t st) {
   return TN_OK;
 }
 
-// builds the grouped-line factors (single mesh) on stream st; the FP64
-// set-up blocks and scratch are freed after
+// builds the grouped-line factors (one mesh, or every mirror of a batch) on
+// stream st; the FP64 set-up blocks and scratch are freed after
 static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
   if (c->gready) return TN_OK;
-  if (is_batch(c)) return fail(TN_EINVAL, "TN_PC_ZGROUP needs a single mesh");
   free_zgroup(c);
+  const int n = is_batch(c) ? c->batch->n : 1;
+  std::vector<const tn::HostMesh *> hms(n);
+  std::vector<DevMesh> dms(n);
+  for (int i = 0; i < n; ++i) {
+    hms[i] = is_batch(c) ? &c->batch->inst[i].hm : &c->hm;
+    dms[i] = is_batch(c) ? c->batch->inst[i].dm : c->dm;
+  }
   char msg[160];
-  if (!tn_zgroup_plan(c->hm, &c->gplan, msg, sizeof(msg))) return fail(TN_EINVAL, "%s", msg);
+  if (!tn_zgroup_plan(hms.data(), n, &c->gplan, msg, sizeof(msg))) return fail(TN_EINVAL, "%s", msg);
   const ZGroupPlan &p = c->gplan;
-  const size_t bb = tn_zline_block_bytes(c->dm), xb = tn_zgroup_cross_bytes(c->dm),
-               wb = tn_zgroup_work_bytes(c->dm, p), fb = (size_t)p.nfac * sizeof(float);
+  size_t bb = 0, xb = 0, wb = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t b1 = tn_zline_block_bytes(dms[i]), x1 = tn_zgroup_cross_bytes(dms[i]),
+                 w1 = tn_zgroup_work_bytes(dms[i], p, i);
+    bb = b1 > bb ? b1 : bb;
+    xb = x1 > xb ? x1 : xb;
+    wb = w1 > wb ? w1 : wb;
+  }
+  const size_t fb = (size_t)p.nfac * sizeof(float);
   double *blk = nullptr, *xblk = nullptr, *work = nullptr;
   cudaError_t e = cudaMalloc((void **)&blk, bb);
   if (e == cudaSuccess) e = cudaMalloc((void **)&xblk, xb);
@@ -320,6 +335,7 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->gstatus, 2 * sizeof(int));  // factor status, solve timeout
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_glines, sizeof(int4) * p.ngroups);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gfac_off, sizeof(long long) * p.ngroups);
+  if (e == cudaSuccess && is_batch(c)) e = cudaMalloc((void **)&c->d_ginst, sizeof(int) * p.ngroups);
   if (e != cudaSuccess) {
     dfree(blk); dfree(xblk); dfree(work);
     free_zgroup(c);
@@ -328,23 +344,32 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
                 cudaGetErrorString(e));
   }
   ZGroupDev &g = c->zgd;
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < kZgSide && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&g.side[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.join[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming);
   g.lines = c->d_glines;
   g.fac_off = c->d_gfac_off;
+  g.inst = is_batch(c) ? c->d_ginst : nullptr;
+  g.meshes = is_batch(c) ? c->batch->d_meshes : nullptr;
+  g.dof_off = is_batch(c) ? c->batch->d_dof_off : nullptr;
   g.ngroups = p.ngroups;
-  for (int k = 0; k <= 4; ++k) { g.cls_start[k] = p.cls_start[k]; g.cls_n[k] = p.cls_n[k]; }
+  g.ncls = p.ncls;
+  for (int k = 0; k < p.ncls; ++k) {
+    g.cls_N[k] = p.cls_N[k]; g.cls_G[k] = p.cls_G[k]; g.cls_start[k] = p.cls_start[k]; g.cls_n[k] = p.cls_n[k];
+  }
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_glines, p.lines.data(), sizeof(int4) * p.ngroups,
                                             cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_gfac_off, p.fac_off.data(), sizeof(long long) * p.ngroups,
                                             cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && is_batch(c))
+    e = cudaMemcpyAsync(c->d_ginst, p.inst.data(), sizeof(int) * p.ngroups, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->gstatus, 0, 2 * sizeof(int), st);
-  if (e == cudaSuccess)
-    e = tn_zgroup_setup(c->dm, p, c->d_glines, c->d_gfac_off, blk, xblk, work, c->gfac, c->gfac64, c->gstatus, st);
+  for (int i = 0; i < n && e == cudaSuccess; ++i)  // one mirror after another (shared set-up scratch)
+    e = tn_zgroup_setup(dms[i], p, i, c->d_glines, c->d_gfac_off, blk, xblk, work, c->gfac, c->gfac64, c->gstatus,
+                        st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->gstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(blk); dfree(xblk); dfree(work);
@@ -904,7 +929,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (o->mode != TN_SOLVE_F64 && o->mode != TN_SOLVE_MIXED_F32) return fail(TN_EINVAL, "unknown solve mode");
   if (o->precond != TN_PC_JACOBI && o->precond != TN_PC_ZLINE && o->precond != TN_PC_ZGROUP)
     return fail(TN_EINVAL, "unknown preconditioner");
-  if (is_batch(c) && o->precond != TN_PC_ZLINE) return fail(TN_EINVAL, "a batch is solved with TN_PC_ZLINE");
+  if (is_batch(c) && o->precond == TN_PC_JACOBI) return fail(TN_EINVAL, "a batch is solved with line blocks");
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
   if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
   if (!(o->energy_rtol >= 0.0)) return fail(TN_EINVAL, "energy_rtol must be >= 0");

@@ -807,11 +807,24 @@ constexpr size_t zg_smem() { return (2 * (size_t)zg_rec(G * 3 * N) + 6 * zg_thre
 // UPD, partial sums and the timeout flag as for single lines.
 template <int N, int G, typename T, bool UPD>
 __global__ void __launch_bounds__(zg_threads<N, G>())
-zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
-                    int gbase, const T *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
-                    T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
-                    double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
+zgroup_solve_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevMesh *__restrict__ meshes,
+                    const long long *__restrict__ dof_off, const int4 *__restrict__ glines,
+                    const long long *__restrict__ gfac, int gbase, const T *__restrict__ fac, T *__restrict__ r,
+                    const T *__restrict__ q, T *__restrict__ z, const double *__restrict__ alpha,
+                    double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
+                    int *__restrict__ err) {
   if (done && *done) return;
+  // one mesh, or a batch: the group's mirror, its mesh and its first unknown
+  int mncol = m1.ncol, mslab = m1.nslab;
+  if (ginst) {
+    const int in = ginst[gbase + blockIdx.x];
+    mncol = meshes[in].ncol;
+    mslab = meshes[in].nslab;
+    const long long o = dof_off[in];
+    r += o;
+    z += o;
+    if (UPD) q += o;
+  }
   constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = zg_threads<N, G>();
   constexpr int LP = zlp(MG), RS = zg_rec(MG);
   extern __shared__ __align__(16) unsigned char zsm[];
@@ -829,8 +842,8 @@ zgroup_solve_kernel(const DevMesh m, const int4 *__restrict__ glines, const long
   const int lid = li == 0 ? L4.x : (li == 1 ? L4.y : (li == 2 ? L4.z : L4.w));
   const int c = lid / N2, qn = lid - c * N2;
   const size_t off = (size_t)k * N2 + qn;
-  const size_t ncol = m.ncol;
-  const int S = m.nslab;
+  const size_t ncol = mncol;
+  const int S = mslab;
   auto gidx = [&](int s) { return ((size_t)(s * ncol + c) * 3 + a) * n + off; };
   const T *base = fac + gfac[grp];
   const T al = UPD ? (T)*alpha : T(0);
@@ -1076,69 +1089,59 @@ cudaError_t solve_batch_n(int prec, const DevMesh *meshes, const int2 *work, int
 }
 
 template <int N>
-cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, const int4 *lines, const long long *fac_off,
-                           double *blk, double *xblk, double *work, float *fac, double *fac64, int *status,
-                           cudaStream_t st) {
+cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
+                           const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
+                           double *fac64, int *status, cudaStream_t st) {
   zline_blocks_kernel<N><<<m.E, ((N * N + 31) / 32) * 32, 0, st>>>(m, blk);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   zgroup_cross_kernel<N><<<m.E, ((4 * N + 31) / 32) * 32, 0, st>>>(m, xblk);
   err = cudaGetLastError();
   for (int g = 1; g <= 4 && err == cudaSuccess; ++g) {
-    if (!p.cls_n[g]) continue;
-    zgroup_factor_kernel<N><<<p.cls_n[g], 128, 0, st>>>(m, lines, fac_off, p.cls_start[g], g, blk, xblk, work,
-                                                         fac, fac64, status);
+    const int cnt = p.inst_n[(size_t)inst * 5 + g];
+    if (!cnt) continue;
+    zgroup_factor_kernel<N><<<cnt, 128, 0, st>>>(m, lines, fac_off, p.inst_start[(size_t)inst * 5 + g], g, blk,
+                                                 xblk, work, fac, fac64, status);
     err = cudaGetLastError();
   }
   return err;
 }
 
 template <int N, int G, typename T, bool UPD>
-cudaError_t zgroup_launch(const DevMesh &m, const ZGroupDev &gd, const void *fac, void *r, const void *q, void *z,
-                          const double *alpha, double *prz, double *prr, const int *done, int *zerr,
+cudaError_t zgroup_launch(const DevMesh &m, const ZGroupDev &gd, int cls, const void *fac, void *r, const void *q,
+                          void *z, const double *alpha, double *prz, double *prr, const int *done, int *zerr,
                           cudaStream_t st) {
   constexpr size_t sm = zg_smem<N, G, T>();
   cudaError_t err = zline_smem_optin(zgroup_solve_kernel<N, G, T, UPD>, sm);
   if (err != cudaSuccess) return err;
-  zgroup_solve_kernel<N, G, T, UPD><<<gd.cls_n[G], zg_threads<N, G>(), sm, st>>>(
-      m, gd.lines, gd.fac_off, gd.cls_start[G], (const T *)fac, (T *)r, (const T *)q, (T *)z, alpha, prz, prr,
-      done, zerr);
+  zgroup_solve_kernel<N, G, T, UPD><<<gd.cls_n[cls], zg_threads<N, G>(), sm, st>>>(
+      m, gd.inst, gd.meshes, gd.dof_off, gd.lines, gd.fac_off, gd.cls_start[cls], (const T *)fac, (T *)r,
+      (const T *)q, (T *)z, alpha, prz, prr, done, zerr);
   return cudaGetLastError();
 }
 
 template <int N, int G>
-cudaError_t zgroup_launch_g(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+cudaError_t zgroup_launch_g(const DevMesh &m, const ZGroupDev &gd, int cls, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *prz, double *prr,
                             const int *done, int *zerr, cudaStream_t st) {
   if (prec == TN_F64)
-    return q ? zgroup_launch<N, G, double, true>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-             : zgroup_launch<N, G, double, false>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-  return q ? zgroup_launch<N, G, float, true>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-           : zgroup_launch<N, G, float, false>(m, gd, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    return q ? zgroup_launch<N, G, double, true>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+             : zgroup_launch<N, G, double, false>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+  return q ? zgroup_launch<N, G, float, true>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+           : zgroup_launch<N, G, float, false>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st);
 }
 
-// the group sizes run concurrently: size 1 on st, sizes 2..4 on side streams
-// forked from and joined back into st (also inside a stream capture)
 template <int N>
-cudaError_t zgroup_solve_n(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
-                           const void *q, void *z, const double *alpha, double *prz, double *prr,
-                           const int *done, int *zerr, cudaStream_t st) {
-  cudaError_t err = cudaEventRecord(gd.fork, st);
-  for (int g = 4; g >= 2 && err == cudaSuccess; --g) {  // the longest chains first
-    if (!gd.cls_n[g]) continue;
-    cudaStream_t sg = gd.side[g - 2];
-    err = cudaStreamWaitEvent(sg, gd.fork, 0);
-    if (err != cudaSuccess) break;
-    if (g == 2) err = zgroup_launch_g<N, 2>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
-    if (g == 3) err = zgroup_launch_g<N, 3>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
-    if (g == 4) err = zgroup_launch_g<N, 4>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, sg);
-    if (err == cudaSuccess) err = cudaEventRecord(gd.join[g - 2], sg);
+cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int cls, int prec, const void *fac, void *r,
+                            const void *q, void *z, const double *alpha, double *prz, double *prr,
+                            const int *done, int *zerr, cudaStream_t st) {
+  switch (gd.cls_G[cls]) {
+    case 1: return zgroup_launch_g<N, 1>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    case 2: return zgroup_launch_g<N, 2>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    case 3: return zgroup_launch_g<N, 3>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    case 4: return zgroup_launch_g<N, 4>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    default: return cudaErrorInvalidValue;
   }
-  if (err == cudaSuccess && gd.cls_n[1])
-    err = zgroup_launch_g<N, 1>(m, gd, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-  for (int g = 2; g <= 4 && err == cudaSuccess; ++g)
-    if (gd.cls_n[g]) err = cudaStreamWaitEvent(st, gd.join[g - 2], 0);
-  return err;
 }
 
 }  // namespace
@@ -1152,7 +1155,9 @@ static int uf_find(std::vector<int> &p, int x) {
   return x;
 }
 
-bool tn_zgroup_plan(const tn::HostMesh &hm, ZGroupPlan *p, char *msg, int msglen) {
+// the groups of one mesh (members ascending), or false if a node is shared
+// by more than 4 columns
+static bool mesh_groups(const tn::HostMesh &hm, std::vector<std::vector<int>> &out, char *msg, int msglen) {
   const int N = hm.N, N2 = N * N, nl = hm.ncol * N2;
   std::vector<int> par(nl);
   for (int x = 0; x < nl; ++x) par[x] = x;
@@ -1171,36 +1176,56 @@ bool tn_zgroup_plan(const tn::HostMesh &hm, ZGroupPlan *p, char *msg, int msglen
       }
     }
   std::vector<std::vector<int>> comp(nl);
-  for (int x = 0; x < nl; ++x) comp[uf_find(par, x)].push_back(x);  // members ascending
-  p->lines.clear();
-  p->fac_off.clear();
-  p->nfac = 0;
-  p->ngroups = 0;
-  for (int g = 0; g <= 4; ++g) { p->cls_start[g] = 0; p->cls_n[g] = 0; }
-  for (int x = 0; x < nl; ++x)
+  for (int x = 0; x < nl; ++x) comp[uf_find(par, x)].push_back(x);
+  out.clear();
+  for (int x = 0; x < nl; ++x) {
+    if (comp[x].empty()) continue;
     if (comp[x].size() > 4) {
       std::snprintf(msg, msglen, "a cross-section node is shared by %d columns (line groups hold at most 4)",
                     (int)comp[x].size());
       return false;
     }
-  const int S = hm.nslab;
-  for (int g = 1; g <= 4; ++g) {
-    p->cls_start[g] = p->ngroups;
-    const long long rec = zg_rec(g * 3 * N);
-    for (int x = 0; x < nl; ++x) {
-      if ((int)comp[x].size() != g) continue;
-      int4 v = make_int4(-1, -1, -1, -1);
-      v.x = comp[x][0];
-      if (g > 1) v.y = comp[x][1];
-      if (g > 2) v.z = comp[x][2];
-      if (g > 3) v.w = comp[x][3];
-      p->lines.push_back(v);
-      p->fac_off.push_back(p->nfac);
-      p->nfac += (long long)S * rec;
-      ++p->cls_n[g];
-      ++p->ngroups;
-    }
+    out.push_back(comp[x]);
   }
+  return true;
+}
+
+bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *p, char *msg, int msglen) {
+  std::vector<std::vector<std::vector<int>>> per(n);
+  for (int i = 0; i < n; ++i)
+    if (!mesh_groups(*hms[i], per[i], msg, msglen)) return false;
+  *p = ZGroupPlan();
+  p->inst_start.assign((size_t)n * 5, 0);
+  p->inst_n.assign((size_t)n * 5, 0);
+  // order: group size (largest first), degree, mirror -- one class per (size, degree)
+  for (int g = 4; g >= 1; --g)
+    for (int N = TN_MIN_N; N <= TN_MAX_N; ++N) {
+      const int start = p->ngroups;
+      for (int i = 0; i < n; ++i) {
+        if (hms[i]->N != N) continue;
+        const long long rec = zg_rec(g * 3 * N);
+        p->inst_start[(size_t)i * 5 + g] = p->ngroups;
+        for (const auto &mm : per[i]) {
+          if ((int)mm.size() != g) continue;
+          p->lines.push_back(make_int4(mm[0], g > 1 ? mm[1] : -1, g > 2 ? mm[2] : -1, g > 3 ? mm[3] : -1));
+          p->inst.push_back(i);
+          p->fac_off.push_back(p->nfac);
+          p->nfac += (long long)hms[i]->nslab * rec;
+          ++p->inst_n[(size_t)i * 5 + g];
+          ++p->ngroups;
+        }
+      }
+      if (p->ngroups == start) continue;
+      if (p->ncls >= kZgMaxCls) {
+        std::snprintf(msg, msglen, "too many line-group classes");
+        return false;
+      }
+      p->cls_N[p->ncls] = N;
+      p->cls_G[p->ncls] = g;
+      p->cls_start[p->ncls] = start;
+      p->cls_n[p->ncls] = p->ngroups - start;
+      ++p->ncls;
+    }
   return true;
 }
 
@@ -1209,37 +1234,63 @@ size_t tn_zgroup_cross_bytes(const DevMesh &m) {
   return (size_t)m.E * 4 * m.N * M * M * sizeof(double);
 }
 
-size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p) {
+size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p, int inst) {
   size_t mx = 0;
   for (int g = 1; g <= 4; ++g) {
-    const size_t MG = (size_t)g * 3 * m.N, b = (size_t)p.cls_n[g] * 3 * MG * MG * sizeof(double);
+    const size_t MG = (size_t)g * 3 * m.N;
+    const size_t b = (size_t)p.inst_n[(size_t)inst * 5 + g] * 3 * MG * MG * sizeof(double);
     mx = b > mx ? b : mx;
   }
   return mx;
 }
 
-cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, const int4 *lines, const long long *fac_off,
-                            double *blk, double *xblk, double *work, float *fac, double *fac64, int *status,
-                            cudaStream_t st) {
+cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
+                            const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
+                            double *fac64, int *status, cudaStream_t st) {
   switch (m.N) {
 #define TN_CASE(NN) \
-    case NN: return zgroup_setup_n<NN>(m, p, lines, fac_off, blk, xblk, work, fac, fac64, status, st);
+    case NN: return zgroup_setup_n<NN>(m, p, inst, lines, fac_off, blk, xblk, work, fac, fac64, status, st);
     TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t tn_zgroup_solve(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+// the classes run concurrently: the first on st, the others round-robin on
+// side streams forked from and joined back into st (also inside a capture)
+cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
                             const int *done, int *zerr, cudaStream_t st) {
-  switch (m.N) {
-#define TN_CASE(NN) \
-    case NN: return zgroup_solve_n<NN>(m, gd, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st);
-    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+  const DevMesh one = m ? *m : DevMesh{};
+  cudaError_t err = cudaEventRecord(gd.fork, st);
+  bool used[kZgSide] = {false};
+  for (int k = 0; k < gd.ncls && err == cudaSuccess; ++k) {
+    cudaStream_t sk = st;
+    if (k > 0) {
+      const int sd = (k - 1) % kZgSide;
+      sk = gd.side[sd];
+      if (!used[sd]) {
+        err = cudaStreamWaitEvent(sk, gd.fork, 0);
+        used[sd] = true;
+        if (err != cudaSuccess) break;
+      }
+    }
+    switch (gd.cls_N[k]) {
+#define TN_CASE(NN)                                                                                        \
+      case NN:                                                                                            \
+        err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, sk); \
+        break;
+      TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
-    default: return cudaErrorInvalidValue;
+      default: err = cudaErrorInvalidValue;
+    }
   }
+  for (int sd = 0; sd < kZgSide && err == cudaSuccess; ++sd) {
+    if (!used[sd]) continue;
+    err = cudaEventRecord(gd.join[sd], gd.side[sd]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, gd.join[sd], 0);
+  }
+  return err;
 }
 
 size_t tn_zline_block_bytes(const DevMesh &m) {

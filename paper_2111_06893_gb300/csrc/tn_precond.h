@@ -29,33 +29,42 @@ cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const i
                                  const int *done, int *zerr, cudaStream_t st);
 
 // ---- line groups: lines joined by matching nodes of lateral faces
+constexpr int kZgMaxCls = 28;  // classes: (group size 1..4) x (N = 3..9)
+constexpr int kZgSide = 6;     // side streams the classes run on
+// the groups of one mesh or of every mirror of a batch, ordered by class
+// (group size, largest first; then N; then mirror)
 struct ZGroupPlan {
   int ngroups = 0;
-  int cls_start[5] = {0, 0, 0, 0, 0};  // groups of g lines: [cls_start[g], cls_start[g] + cls_n[g])
-  int cls_n[5] = {0, 0, 0, 0, 0};
-  std::vector<int4> lines;          // per group: line ids col * N^2 + j * N + i (-1: unused)
+  std::vector<int4> lines;          // per group: line ids col * N^2 + j * N + i of its mirror (-1: unused)
+  std::vector<int> inst;            // per group: mirror
   std::vector<long long> fac_off;   // per group: first factor entry
   long long nfac = 0;               // factor entries in all
+  int ncls = 0;
+  int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
+  std::vector<int> inst_start, inst_n;  // [mirror * 5 + g]: first group and count of size g (set-up)
 };
-// device view of a plan and the streams the group sizes run on
+// device view of a plan and the streams the classes run on
 struct ZGroupDev {
   const int4 *lines = nullptr;
   const long long *fac_off = nullptr;
-  int ngroups = 0;
-  int cls_start[5] = {0, 0, 0, 0, 0};
-  int cls_n[5] = {0, 0, 0, 0, 0};
-  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+  const int *inst = nullptr;           // batch: mirror of every group (nullptr: one mesh)
+  const DevMesh *meshes = nullptr;     // batch: meshes of the mirrors (device)
+  const long long *dof_off = nullptr;  // batch: first unknown of every mirror (device)
+  int ngroups = 0, ncls = 0;
+  int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
+  cudaStream_t side[kZgSide] = {nullptr};
+  cudaEvent_t fork = nullptr, join[kZgSide] = {nullptr};
 };
-bool tn_zgroup_plan(const tn::HostMesh &hm, ZGroupPlan *plan, char *msg, int msglen);
-size_t tn_zgroup_cross_bytes(const DevMesh &m);                      // FP64 cross-line blocks (set-up)
-size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p);  // FP64 factorisation scratch (set-up)
-// blk: tn_zline_block_bytes; fac / fac64: plan.nfac entries; *status = 1 on a
-// non-positive pivot
-cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, const int4 *lines, const long long *fac_off,
-                            double *blk, double *xblk, double *work, float *fac, double *fac64, int *status,
-                            cudaStream_t st);
-// as tn_zline_solve, over the groups; partial sums: one per group
-cudaError_t tn_zgroup_solve(const DevMesh &m, const ZGroupDev &gd, int prec, const void *fac, void *r,
+bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *plan, char *msg, int msglen);
+size_t tn_zgroup_cross_bytes(const DevMesh &m);                                // FP64 cross-line blocks (set-up)
+size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p, int inst);  // FP64 scratch (set-up)
+// factors of mirror `inst` (its mesh m); blk: tn_zline_block_bytes(m);
+// fac / fac64: plan.nfac entries; *status = 1 on a non-positive pivot
+cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
+                            const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
+                            double *fac64, int *status, cudaStream_t st);
+// as tn_zline_solve, over the groups (m: the mesh, nullptr for a batch);
+// partial sums: one per group
+cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
                             const int *done, int *zerr, cudaStream_t st);

@@ -31,7 +31,7 @@ struct OpSys {
   int n_apply_parts = 0;  // partial sums written by one apply
   int n_rz_parts = 0;     // partial sums of r.z written by one z-line solve (r.r: as many, after them)
   int *zerr = nullptr;    // set to 1 by a z-line solve whose staging wait ran out
-  bool grouped = false;   // single mesh: grouped lines (zg) instead of single lines
+  bool grouped = false;   // grouped lines (zg) instead of single lines
   ZGroupDev zg;
   cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const;
   // z = M^{-1} r; q != nullptr: first r <- r - (*alpha) q.  part: n_rz_parts

@@ -288,10 +288,8 @@ class Context:
         return o
 
     def _precond(self, precond):
-        """None: grouped lines for a single mirror, single lines for a batch."""
-        if precond is not None:
-            return precond
-        return "zline" if getattr(self, "descs", None) is not None else "zgroup"
+        """None: grouped lines (one mirror or a batch)."""
+        return "zgroup" if precond is None else precond
 
     def precond_factor_bytes(self, precond=None):
         """FP32 factor bytes one FP32 application of the preconditioner reads."""
@@ -336,10 +334,9 @@ class Context:
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond=None,
               energy_rtol=0.0, inner_max=None, fcg_window=16):
-        """precond None: grouped lines for one mirror, single lines for a
-        batch.  inner_max None: 100 FP32 iterations per flexible-CG step with
-        grouped lines, 300 with single lines (measured best on the 2.0 M DOF
-        single-coating mirror)."""
+        """precond None: grouped lines.  inner_max None: 100 FP32 iterations
+        per flexible-CG step with grouped lines, 300 with single lines
+        (measured best on the 2.0 M DOF single-coating mirror)."""
         precond = self._precond(precond)
         if inner_max is None:
             inner_max = 100 if precond == "zgroup" else 300

@@ -36,26 +36,29 @@ def test_batch_blocks_equal_single_mirror_results():
         u = torch.tensor(rng.uniform(-1, 1, size=int(off[-1])), dtype=dtype, device="cuda")
         y = bc.apply_operator(u)
         z = bc.precond_apply(u, precond="zline")
+        zg = bc.precond_apply(u, precond="zgroup")
         for i, d in enumerate(descs):
             sc = thermonoise.setup(d)
             ui = u[off[i]:off[i + 1]].clone()
             assert torch.equal(y[off[i]:off[i + 1]], sc.apply_operator(ui)), (i, dtype)
             assert torch.equal(z[off[i]:off[i + 1]], sc.precond_apply(ui, precond="zline")), (i, dtype)
+            assert torch.equal(zg[off[i]:off[i + 1]], sc.precond_apply(ui, precond="zgroup")), (i, dtype)
 
 
 def test_batched_solve_energies_match_oracle():
     from paper_2111_06893_gb300 import thermonoise
     descs = batch_descs()[:4]
     bc = thermonoise.Context().build_batch(descs)
-    for mode in ("f64", "mixed"):
-        u, rep = bc.solve(mode=mode, rtol=1e-12, energy_rtol=1e-12)
+    Uos = []
+    for d in descs:
+        op = Operator(Mesh(d))
+        Uos.append(ob.layer_energies(op, ob.solve_dense(op.assemble(), op.rhs())))
+    for mode, pc in (("f64", "zline"), ("mixed", "zline"), ("f64", "zgroup"), ("mixed", "zgroup")):
+        u, rep = bc.solve(mode=mode, rtol=1e-12, energy_rtol=1e-12, precond=pc)
         U = bc.layer_energies(u)
-        for i, d in enumerate(descs):
-            op = Operator(Mesh(d))
-            A = op.assemble()
-            Uo = ob.layer_energies(op, ob.solve_dense(A, op.rhs()))
+        for i, Uo in enumerate(Uos):
             Ui = U[bc.layer_off[i]:bc.layer_off[i + 1]]
-            assert np.max(np.abs(Ui - Uo) / Uo) < 1e-9, (mode, i, Ui, Uo, rep)
+            assert np.max(np.abs(Ui - Uo) / Uo) < 1e-9, (mode, pc, i, Ui, Uo, rep)
 
 
 def test_batched_gradients_equal_single_mirror_gradients():
