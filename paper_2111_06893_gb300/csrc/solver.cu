@@ -608,7 +608,7 @@ cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStr
 cudaError_t OpSys::zsolve(int prec, const void *fac, void *r, const void *q, void *z, const double *alpha,
                           double *part, const int *done, cudaStream_t st) const {
   double *prr = part ? part + n_rz_parts : nullptr;
-  if (m && grouped) return tn_zgroup_solve(*m, zg, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
+  if (grouped) return tn_zgroup_solve(m, zg, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
   if (m) return tn_zline_solve(*m, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
   for (int g = 0; g < ngroups; ++g) {
     cudaError_t e = tn_zline_solve_batch(gN[g], prec, meshes, gline[g], glines[g], fac_off, dof_off, fac, r, q, z,
