@@ -59,7 +59,7 @@ def fp32_apply_flops_per_dof(N):
 # of `bench.py --mode apply --workload single_coating`; absent where no
 # capture of the current kernels exists
 ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, one launch per (N, G) class on concurrent streams"):
-                 (43.241984 + 0.001536 + 2.476544 + 131.687168 + 4.2112 + 101.7792 + 3.5136) * 1e6}
+                 (43236096 + 512 + 2476544 + 0 + 131932160 + 996608 + 102644224 + 581376) * 1.0}
 
 
 def measured_peaks():

@@ -403,12 +403,12 @@ template <typename T>
 static cudaError_t pcg_iteration(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                  double *part_elem, double *part_red, cudaStream_t st) {
   TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
-  k_alpha<<<1, 256, 0, st>>>(s, part_elem, sys.n_apply_parts);
+  k_alpha<<<1, 1024, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
   k_update<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (T *)v.z, (const T *)v.p,
                                                   (const T *)v.q, (const T *)v.dinv, part_red);
   TN_CU(cudaGetLastError());
-  k_beta<<<1, 256, 0, st>>>(s, part_red, kRedBlocks);
+  k_beta<<<1, 1024, 0, st>>>(s, part_red, kRedBlocks);
   TN_CU(cudaGetLastError());
   k_pupdate<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
@@ -418,11 +418,11 @@ template <typename T>
 static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                        double *part_elem, double *part_red, cudaStream_t st) {
   TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
-  k_alpha<<<1, 256, 0, st>>>(s, part_elem, sys.n_apply_parts);
+  k_alpha<<<1, 1024, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
   // r -= alpha q fused into the line solve (partials r.z and r.r)
   TN_CU(sys.zsolve(prec, v.zfac, v.r, v.q, v.z, &s->alpha, v.part_rz, &s->done, st));
-  k_beta_split<<<1, 256, 0, st>>>(s, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts, sys.n_rz_parts);
+  k_beta_split<<<1, 1024, 0, st>>>(s, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts, sys.n_rz_parts);
   TN_CU(cudaGetLastError());
   k_pupdate_x<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
