@@ -125,6 +125,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_over_ranks(t_local, applies, dist, device):
+    """Whole-job figures of a replicas run (every rank solves its own
+    mirror): the slowest rank's time and the operator applies of all ranks."""
+    import torch
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    aa = torch.tensor([float(applies)], dtype=torch.float64, device=device)
+    dist.all_reduce(aa, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(aa.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -348,12 +359,7 @@ def main():
     tot_applies = applies
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        aa = torch.tensor([applies], dtype=torch.float64, device=dev)
-        dist.all_reduce(aa, op=dist.ReduceOp.SUM)
-        tot_applies = float(aa.item())
+        t_max, tot_applies = aggregate_over_ranks(t_local, applies, dist, dev)
     value = tot_applies * ndof / t_max / 1e9
     mixed_s = t_local / args.steps
 
