@@ -13,8 +13,10 @@ mixed and the plain FP64 solve, the roofline of the dominant kernel of the
 step (the FP32 column-line solve, HBM-bound) and of the FP32 apply
 (ALU-bound), and the FP64 oracle on the host cores.
 
-Multi-GPU: replicas only (every rank solves its own mirror; no collective on
-the data path); value = all ranks' DOF-applies / max over ranks of the time.
+Multi-GPU: no collective on the data path.  A single-mirror workload runs
+as replicas (every rank solves its own copy); the design sweep gives every
+rank its own 256 mirrors (different seeds).  value = all ranks' DOF-applies
+/ max over ranks of the time (weak scaling).
 `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
 """
 import argparse
@@ -227,7 +229,11 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    desc = WORKLOADS[args.workload]()
+    if args.workload == "design_sweep":
+        # independent mirrors: every rank solves its own 256 (mirrors 256 r .. 256 r + 255)
+        desc = W.design_sweep(256, first=256 * rank)
+    else:
+        desc = WORKLOADS[args.workload]()  # one mirror: every rank solves its own copy
     descs = desc if isinstance(desc, list) else [desc]
     batched = isinstance(desc, list)
     if batched:

@@ -177,8 +177,9 @@ def sweep_instance(seed):
                     p, 4, r0=r0)
 
 
-def design_sweep(n=256):
-    return [sweep_instance(s) for s in range(n)]
+def design_sweep(n=256, first=0):
+    """Mirrors first .. first + n - 1 of the seeded sweep."""
+    return [sweep_instance(s) for s in range(first, first + n)]
 
 
 def random_field(desc, seed=0):
