@@ -174,7 +174,22 @@ def oracle_sample_rate(desc, budget_s, max_elems=64):
     return done * 3 * m.n / dt / 1e9, done, dt, threads
 
 
-def run_reference(args, desc, world, rank):
+def bench_config(args, descs, world):
+    """The `config` of the JSON line, the same for both arms."""
+    batched = len(descs) > 1 or args.workload == "design_sweep"
+    pc = args.precond or "zgroup"
+    return {"workload": args.workload, "ndof": sum(W.n_dof(d) for d in descs),
+            "degree": sorted({d["degree"] for d in descs}) if batched else descs[0]["degree"],
+            "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
+            "step": "rhs+mixed solve+energies+psd",
+            "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
+            "inner_max": args.inner_max or (100 if pc == "zgroup" else 300),
+            "fcg_window": args.fcg_window,
+            "precond": pc, "l2": "flushed between steps (256 MB)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def run_reference(args, desc, world, rank, descs=None):
     if rank != 0:
         return
     times = []
@@ -192,8 +207,7 @@ def run_reference(args, desc, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "ndof": W.n_dof(desc), "degree": desc["degree"],
-                   "elements": W.n_elements(desc)},
+        "config": bench_config(args, descs or [desc], world),
         "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
                          "sample": f"FP64 oracle element rows of A u (explicit element matrices, N={N}) "
                                    f"for up to {args.ref_step_s:.0f} s of elements per step"},
@@ -239,7 +253,7 @@ def main():
     if batched:
         desc = descs[0]  # the CPU oracle samples the first mirror of a batch
     if args.impl == "reference":
-        run_reference(args, desc, world, rank)
+        run_reference(args, desc, world, rank, descs)
         return
 
     import torch
@@ -468,15 +482,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "ndof": ndof,
-                   "degree": sorted({d["degree"] for d in descs}) if batched else desc["degree"],
-                   "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
-                   "step": "rhs+mixed solve+energies+psd",
-                   "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
-                   "inner_max": args.inner_max or (100 if pc == "zgroup" else 300),
-                   "fcg_window": args.fcg_window,
-                   "precond": pc, "l2": "flushed between steps (256 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": bench_config(args, descs, world),
         "time_to_U_s": {"mixed": mixed_s, "fp64": t_fp64,
                         "mixed_energy_rel_err": err_mixed,
                         "fp64_energy_rel_err": err64 if t_fp64 is not None else None},
