@@ -1,4 +1,4 @@
-// Column-line block preconditioner for thin layers.
+// Column-line and grouped-line block preconditioners for thin layers.
 //
 // The paper accelerates its Krylov solver with multigrid and an additive
 // Schwarz smoother (Sec. 2.3).  The dominant difficulty of thin coating layers
@@ -13,7 +13,9 @@
 // same weak-form terms as the operator (FP64), factorised by block Cholesky
 // along the line (one thread per line) and stored in FP32.  Application:
 // one warp per line, the 3N unknowns of a slab on the lanes, forward and
-// backward block substitution.
+// backward block substitution.  The grouped variant (further below) takes
+// the lines through one cross-section point of neighbouring columns
+// together, adding the lateral-face coupling between them.
 #include <cstdio>
 #include <vector>
 
