@@ -64,6 +64,11 @@ ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, one launc
                  (43236096 + 512 + 2476544 + 0 + 131932160 + 996608 + 102644224 + 581376) * 1.0}
 
 
+# DRAM bytes (read + write) of one FP32 apply, from `ncu --set full -k
+# regex:apply2_kernel` of `bench.py --mode apply --workload single_coating`
+APPLY_TRAFFIC = {("single_coating", "apply2_kernel<7,float>"): 8144128.0}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -536,7 +541,8 @@ def main():
                      "algorithmic_bytes": zbytes,
                      "peak_source": peak_src},
         "roofline_apply": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                           "frac": achieved / peak_fp32, "traffic": None,
+                           "frac": achieved / peak_fp32,
+                           "traffic": None if batched else APPLY_TRAFFIC.get((args.workload, f"apply2_kernel<{N},float>")),
                            "kernel": "apply2_batch_kernel<N,float>" if batched else f"apply2_kernel<{N},float>",
                            "flops_per_dof": flops_dof,
                            "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
