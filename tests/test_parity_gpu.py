@@ -271,6 +271,86 @@ def test_single_coating_full_size_sampled_rows():
         assert err32 < 2e-5, (e, err32)
 
 
+def test_single_coating_full_size_sampled_line_groups():
+    """The grouped-line solve on the 2.0 M DOF mirror: for one group of each
+    size (1 to 4 lines), z = A_GG^-1 r against the group's principal
+    sub-matrix assembled from the oracle's element rows; and the whole
+    preconditioner is symmetric positive definite at full size."""
+    from scipy.spatial import cKDTree
+    desc = W.single_coating()
+    ctx = gpu_ctx(desc)
+    m = Mesh(desc)
+    op = Operator(m)
+    N, n, S = m.N, m.n, m.nslab
+    r = W.random_field(desc, 31)
+    z = ctx.precond_apply(to_dev(r), precond="zgroup").cpu().numpy()
+    z32 = ctx.precond_apply(to_dev(r, torch.float32), precond="zgroup").cpu().numpy().astype(np.float64)
+    # groups of lines by the physical position of their nodes
+    lines, pts = [], []
+    for c in range(m.ncol):
+        xyz = np.real(m.geometry(c)["xyz"])
+        for j in range(N):
+            for i in range(N):
+                lines.append((c, i, j))
+                pts.append(xyz[j * N + i][:2])
+    pts = np.array(pts)
+    parent = list(range(len(pts)))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for a, b in cKDTree(pts).query_pairs(1e-9 * max(1.0, float(np.abs(pts).max()))):
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    groups = {}
+    for t_ in range(len(pts)):
+        groups.setdefault(find(t_), []).append(lines[t_])
+    pick = {}
+    for g in groups.values():
+        pick.setdefault(len(g), g)
+    assert sorted(pick) == [1, 2, 3, 4]
+    cache = {}
+
+    def rows(e):
+        if e not in cache:
+            cache[e] = op.element_rows(e)
+        return cache[e]
+
+    for g, members in sorted(pick.items()):
+        # DOFs of the group: line, slab, component, k
+        idx, per_elem = [], {}  # per_elem[e] = (local indices in e, positions in the group)
+        for (c, i, j) in members:
+            for s in range(S):
+                e = s * m.ncol + c
+                for comp in range(3):
+                    for k in range(N):
+                        loc = comp * n + (k * N + j) * N + i
+                        per_elem.setdefault(e, ([], []))
+                        per_elem[e][0].append(loc)
+                        per_elem[e][1].append(len(idx))
+                        idx.append(e * 3 * n + loc)
+        B = np.zeros((len(idx), len(idx)))
+        for e, (locs, pos) in per_elem.items():
+            for e2, blk in rows(e).items():
+                if e2 in per_elem:
+                    locs2, pos2 = per_elem[e2]
+                    B[np.ix_(pos, pos2)] = blk[np.ix_(locs, locs2)]
+        idx = np.array(idx)
+        bwd = np.abs(B @ z[idx] - r[idx]).max() / (np.abs(B).max() * np.abs(z[idx]).max())
+        bwd32 = np.abs(B @ z32[idx] - r[idx]).max() / (np.abs(B).max() * np.abs(z32[idx]).max())
+        assert bwd < 1e-13, (g, bwd)
+        assert bwd32 < 1e-5, (g, bwd32)
+    # symmetric positive definite: (M^-1 a) . b = a . (M^-1 b), a . M^-1 a > 0
+    a = W.random_field(desc, 32)
+    za = ctx.precond_apply(to_dev(a), precond="zgroup").cpu().numpy()
+    assert abs(za @ r - a @ z) <= 1e-10 * np.sqrt((za @ a) * (z @ r))
+    assert za @ a > 0 and z @ r > 0
+
+
 def test_invalid_arguments_are_rejected_before_launch():
     from paper_2111_06893_gb300 import thermonoise
     desc = CASES["box_tiny_p2"]()
