@@ -351,6 +351,32 @@ def test_single_coating_full_size_sampled_line_groups():
     assert za @ a > 0 and z @ r > 0
 
 
+def test_single_coating_full_size_sampled_element_energies():
+    """Layer energies on the 2.0 M DOF mirror for a field that is nonzero on a
+    few sampled elements only: each layer's energy is then the sum of those
+    elements' energies, which the oracle computes element by element."""
+    desc = W.single_coating()
+    ctx = gpu_ctx(desc)
+    m = Mesh(desc)
+    op = Operator(m)
+    nl = 3 * m.n
+    rng = np.random.default_rng(5)
+    sample = sorted(set([0, m.ncol - 1, m.ncol + 3, m.E - 1] + rng.integers(0, m.E, size=6).tolist()))
+    full = W.random_field(desc, 12)
+    u = np.zeros_like(full)
+    for e in sample:
+        u[e * nl:(e + 1) * nl] = full[e * nl:(e + 1) * nl]
+    U = ctx.layer_energies(to_dev(u))
+    Uo = np.zeros_like(U)
+    for e in sample:
+        Uo[m.layer(e)] += ob.element_energy(op, e, u)
+    for L in range(len(U)):
+        if Uo[L] == 0.0:
+            assert U[L] == 0.0
+        else:
+            assert abs(U[L] - Uo[L]) <= 1e-12 * abs(Uo[L]), (L, U[L], Uo[L])
+
+
 def test_invalid_arguments_are_rejected_before_launch():
     from paper_2111_06893_gb300 import thermonoise
     desc = CASES["box_tiny_p2"]()
