@@ -188,7 +188,7 @@ def bench_config(args, descs, world):
             "elements": sum(W.n_elements(d) for d in descs), "mirrors": len(descs),
             "step": "rhs+mixed solve+energies+psd",
             "rtol": args.rtol, "energy_rtol": args.energy_rtol, "inner_rtol": args.inner_rtol,
-            "inner_max": args.inner_max or (100 if pc == "zgroup" else 300),
+            "inner_max": args.inner_max or (40 if pc == "zgroup" else 300),
             "fcg_window": args.fcg_window,
             "precond": pc, "l2": "flushed between steps (256 MB)",
             "parallelism": "replicas" if world > 1 else "single"}
@@ -233,7 +233,7 @@ def main():
                     help="stop once every U_i changes by less than this between checks")
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--inner-max", type=int, default=None,
-                    help="default: 100 with grouped lines, 300 with single lines")
+                    help="default: 40 with grouped lines, 300 with single lines")
     ap.add_argument("--fcg-window", type=int, default=16)
     ap.add_argument("--precond", default=None, choices=["zline", "zgroup", "jacobi"],
                     help="default: grouped lines")

@@ -186,7 +186,7 @@ typedef struct {
   int max_outer;
   int use_x0;
   int check_every;          /* iterations between host convergence checks */
-  int inner_max;            /* mixed: FP32 PCG iterations per outer step (0: 300; 100 is faster with TN_PC_ZGROUP) */
+  int inner_max;            /* mixed: FP32 PCG iterations per outer step (0: 40 with TN_PC_ZGROUP, else 300) */
   int fcg_window;           /* mixed: directions kept by the flexible CG (0 or max: 16) */
   double energy_rtol;       /* > 0: also stop once every layer energy U_i
                                changes by <= energy_rtol (relative) between

@@ -1005,7 +1005,9 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   } else {
     if (!is_batch(c)) CU_TRY(tn::pcg_setup_dinv(n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
     const int m = o->fcg_window > 0 ? (o->fcg_window > 16 ? 16 : o->fcg_window) : 16;
-    const int kin = o->inner_max > 0 ? o->inner_max : 300;
+    // default inner length: grouped lines reach the energy test fastest with
+    // short inner runs (the flexible CG keeps the directions across them)
+    const int kin = o->inner_max > 0 ? o->inner_max : (o->precond == TN_PC_ZGROUP ? 40 : 300);
     if ((st = ensure_fcg(c, m))) return st;
     double *P0 = c->fcg, *AP0 = c->fcg + (size_t)m * n;
     // r = b - A x

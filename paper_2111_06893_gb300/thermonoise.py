@@ -284,6 +284,7 @@ class Context:
         o.rtol, o.inner_rtol = rtol, inner_rtol
         o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
         o.energy_rtol = energy_rtol
+        o.inner_max = 300  # adjoint solves: inner runs stop at inner_rtol; 300 only bounds them
         o.use_x0 = 0
         return o
 
@@ -334,19 +335,18 @@ class Context:
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond=None,
               energy_rtol=0.0, inner_max=None, fcg_window=16):
-        """precond None: grouped lines.  inner_max None: 100 FP32 iterations
-        per flexible-CG step with grouped lines, 300 with single lines
-        (measured best on the 2.0 M DOF single-coating mirror)."""
+        """precond None: grouped lines.  inner_max None: the library's
+        default, 40 FP32 iterations per flexible-CG step with grouped lines
+        and 300 otherwise (measured best on the single-coating, crystalline
+        and design-sweep workloads)."""
         precond = self._precond(precond)
-        if inner_max is None:
-            inner_max = 100 if precond == "zgroup" else 300
         o = SolveOpts()
         o.mode = TN_SOLVE_F64 if mode == "f64" else TN_SOLVE_MIXED_F32
         o.precond = PRECONDS[precond]
         o.rtol, o.inner_rtol = rtol, inner_rtol
         o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
         o.energy_rtol = energy_rtol
-        o.inner_max, o.fcg_window = inner_max, fcg_window
+        o.inner_max, o.fcg_window = inner_max or 0, fcg_window
         u = out if out is not None else self._vec(self._torch.float64)
         o.use_x0 = 0
         if x0 is not None:
