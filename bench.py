@@ -407,6 +407,7 @@ def main():
         return e0.elapsed_time(e1) / reps_n / 1e3
 
     t32 = time_apply(x32, y32, 200)
+    tuning = ctx.apply_tuning()  # FP32 operator variant per degree, timed by the first FP32 call
     t64 = time_apply(x64, y64, 20)
 
     # the dominant kernel of the step: the FP32 preconditioner solve (column lines)
@@ -533,7 +534,8 @@ def main():
                   "reference_iters": rep_ref["inner_iters"], "reference_rel_residual": rep_ref["rel_residual"],
                   "reference_status": rep_ref["status"]},
         "apply_kernel": {"f32_us": t32 * 1e6, "f64_us": t64 * 1e6,
-                         "f32_gdofs": ndof / t32 / 1e9, "f64_gdofs": ndof / t64 / 1e9},
+                         "f32_gdofs": ndof / t32 / 1e9, "f64_gdofs": ndof / t64 / 1e9,
+                         "autotune": {f"p{p}": v for p, v in tuning.items()}},
         "roofline": {"bound": "hbm", "achieved": zbytes / tz / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": zbytes / tz / 1e9 / hbm_peak,
                      "traffic": ZLINE_TRAFFIC.get((args.workload, zkernel)),

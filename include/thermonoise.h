@@ -129,6 +129,26 @@ tn_status tn_set_beam(tn_ctx *ctx, double r0, double F0);
  * and must be 16-byte aligned. */
 tn_status tn_apply_operator(tn_ctx *ctx, int precision, const void *u_dev, void *y_dev);
 
+/* Autotuning of the FP32 operator kernel (the element-wise apply of
+ * Eq. (dg_residuals)).  Two builds of it differ only in the resident CTAs
+ * per SM asked of the register allocator: variant 0 gives every thread the
+ * registers the code needs, variant 1 one CTA more per SM with fewer
+ * registers per thread.  They execute the same arithmetic in the same
+ * order, so results are bit-identical.  The first tn_apply_operator
+ * (TN_F32) or mixed-mode tn_solve after a mesh or batch is built times both
+ * for every degree present (3 + 10 launches of each, CUDA events on the
+ * stream of the call, not while it is being captured; the call's y, or the
+ * solver's FP32 workspace, is overwritten meanwhile) and keeps variant 1
+ * only when it is faster by more than 2 %.
+ * tn_apply_tuning: variant[p - 2] for p = 2..8 is 0 or 1 once settled, -1
+ * before; us (may be NULL) receives 14 doubles, the time per launch in
+ * microseconds of variants 0 and 1 for each degree (0 where not timed).
+ * tn_set_apply_variant fixes the variant of one degree (0 or 1; the
+ * autotuner then leaves it alone) or, with -1, lets it be timed again.
+ * Building a mesh or batch resets both. */
+tn_status tn_apply_tuning(const tn_ctx *ctx, int *variant, double *us);
+tn_status tn_set_apply_variant(tn_ctx *ctx, int degree, int variant);
+
 /* b of A u = b (Eq. (matrix_eqn)) for the beam load: b = -sum over top-face
  * nodes of w^S J^S p(r) e_z (Neumann data of Eq. (bc)).  FP64, ndof values. */
 tn_status tn_rhs(tn_ctx *ctx, double *b_dev);

@@ -123,6 +123,12 @@ struct tn_ctx {
   double *gpart = nullptr;
   int *gstatus = nullptr;
   bool gready = false;
+  // FP32 operator kernel, per LGL count N (index N): the occupancy variant in
+  // use, whether it is settled (timed, or fixed by the caller), and the time
+  // per launch measured for variants 0 and 1; reset with the mesh
+  int apply_var[10] = {0};
+  bool apply_set[10] = {false};
+  float apply_us[10][2] = {};
 };
 
 static void free_zline(tn_ctx *c) {
@@ -160,8 +166,17 @@ static int total_layers(const tn_ctx *c);
 static int apply_parts(const tn_ctx *c);
 static bool is_batch(const tn_ctx *c);
 
+static void reset_tuning(tn_ctx *c) {
+  for (int N = 0; N < 10; ++N) {
+    c->apply_var[N] = 0;
+    c->apply_set[N] = false;
+    c->apply_us[N][0] = c->apply_us[N][1] = 0.0f;
+  }
+}
+
 static void free_mesh(tn_ctx *c) {
   free_precond(c);
+  reset_tuning(c);
   dfree(c->d_colgeo);
   dfree(c->d_slabgeo);
   dfree(c->d_colnb);
@@ -471,13 +486,43 @@ static OpSys make_sys(const tn_ctx *c) {
   OpSys s;
   if (is_batch(c)) {
     s = c->batch->sys;
+    for (int g = 0; g < s.ngroups; ++g) s.gvar[g] = c->apply_var[s.gN[g]];
   } else {
     s.m = &c->dm;
+    s.mvar = c->apply_var[c->dm.N];
     s.n_apply_parts = c->dm.E;
     s.n_rz_parts = tn_zline_partials(c->dm);
   }
   s.zerr = c->zstatus ? c->zstatus + 1 : nullptr;
   return s;
+}
+
+// Autotuner of the FP32 operator kernel: for every LGL count of the context
+// (the mesh, or each degree group of a batch) not yet settled, times both
+// occupancy variants on the vectors u -> y (y is overwritten) and keeps
+// variant 1 only when it is faster by more than 2 %.  Nothing is timed while
+// st is being captured into a graph.
+static tn_status ensure_tuned(tn_ctx *c, const float *u, float *y, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CU_TRY(cudaStreamIsCapturing(st, &cs), "capture status");
+  if (cs != cudaStreamCaptureStatusNone) return TN_OK;
+  const bool batch = is_batch(c);
+  const OpSys s = make_sys(c);
+  const int ng = batch ? s.ngroups : 1;
+  for (int g = 0; g < ng; ++g) {
+    const int N = batch ? s.gN[g] : c->dm.N;
+    if (N < 3 || N > 9 || c->apply_set[N]) continue;
+    float us[2] = {0.0f, 0.0f};
+    if (batch)
+      CU_TRY(tn_tune_apply(nullptr, N, s.meshes, s.gwork[g], s.gcount[g], s.dof_off, u, y, st, us), "tuning");
+    else
+      CU_TRY(tn_tune_apply(&c->dm, N, nullptr, nullptr, 0, nullptr, u, y, st, us), "tuning");
+    c->apply_us[N][0] = us[0];
+    c->apply_us[N][1] = us[1];
+    c->apply_var[N] = us[1] < 0.98f * us[0] ? 1 : 0;
+    c->apply_set[N] = true;
+  }
+  return TN_OK;
 }
 
 static int total_layers(const tn_ctx *c) { return is_batch(c) ? c->batch->n_layers : c->dm.n_layers; }
@@ -890,7 +935,32 @@ tn_status tn_apply_operator(tn_ctx *c, int precision, const void *u, void *y) {
   const char *a = (const char *)u, *b = (const char *)y;
   const size_t bytes = c->ndof * es;
   if (a < b + bytes && b < a + bytes) return fail(TN_EINVAL, "u and y overlap");
+  if (precision == TN_F32 && (st = ensure_tuned(c, (const float *)u, (float *)y, c->stream))) return st;
   CU_TRY(make_sys(c).apply(precision, u, y, nullptr, c->stream), "apply launch");
+  return TN_OK;
+}
+
+tn_status tn_apply_tuning(const tn_ctx *c, int *variant, double *us) {
+  if (!c || !variant) return fail(TN_EINVAL, "null argument");
+  for (int p = 2; p <= 8; ++p) {
+    const int N = p + 1;
+    variant[p - 2] = c->apply_set[N] ? c->apply_var[N] : -1;
+    if (us) {
+      us[2 * (p - 2)] = c->apply_us[N][0];
+      us[2 * (p - 2) + 1] = c->apply_us[N][1];
+    }
+  }
+  return TN_OK;
+}
+
+tn_status tn_set_apply_variant(tn_ctx *c, int degree, int variant) {
+  if (!c) return fail(TN_EINVAL, "null context");
+  if (degree < 2 || degree > 8) return fail(TN_EINVAL, "degree must be in 2..8");
+  if (variant < -1 || variant > 1) return fail(TN_EINVAL, "variant must be -1, 0 or 1");
+  const int N = degree + 1;
+  c->apply_var[N] = variant < 0 ? 0 : variant;
+  c->apply_set[N] = variant >= 0;
+  c->apply_us[N][0] = c->apply_us[N][1] = 0.0f;
   return TN_OK;
 }
 
@@ -1003,6 +1073,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
     }
     r.status = energy_done ? 1 : 0;
   } else {
+    if ((st = ensure_tuned(c, c->p32, c->q32, s))) return st;
     if (!is_batch(c)) CU_TRY(tn::pcg_setup_dinv(n, c->diag64, c->dinv32, TN_F32, s), "dinv32");
     const int m = o->fcg_window > 0 ? (o->fcg_window > 16 ? 16 : o->fcg_window) : 16;
     // default inner length: grouped lines reach the energy test fastest with

@@ -854,25 +854,30 @@ __device__ __forceinline__ void apply2_body(const DevMesh &m, const int e, const
 }
 
 // resident CTAs per SM requested from the register allocator for the
-// line-task kernel (FP32, N <= 7: four CTAs of nthreads<N>() threads)
-template <int N, typename T>
+// line-task kernel.  Variant 0: FP32, the CTAs per SM that fit ~60 registers
+// per thread (N = 7: three CTAs of 352 threads); FP64: one.  Variant 1
+// (FP32 only): one CTA more per SM than the registers of variant 0 allow,
+// within the shared-memory limit (N = 3: 32, 4: 16, 5: 8, 6: 5, 7: 4, 8: 3,
+// 9: 2), paid for with fewer registers per thread.  The two variants run the
+// same instructions in the same order, so their results are bit-identical;
+// the autotuner below times both on the mesh at hand.
+template <int N, typename T, int V>
 __host__ __device__ constexpr int apply2_min_blocks() {
-  // FP32: the CTAs per SM that fit ~60 registers per thread (N = 7: three
-  // CTAs of 352 threads; forcing four spills and runs slower); FP64: one
   if (sizeof(T) != 4) return 1;
-  return N <= 4 ? 8 : (N == 5 ? 6 : (N == 6 ? 4 : (N == 7 ? 3 : (N == 8 ? 2 : 1))));
+  if (V == 0) return N <= 4 ? 8 : (N == 5 ? 6 : (N == 6 ? 4 : (N == 7 ? 3 : (N == 8 ? 2 : 1))));
+  return N == 3 ? 32 : (N == 4 ? 16 : (N == 5 ? 8 : (N == 6 ? 5 : (N == 7 ? 4 : (N == 8 ? 3 : 2)))));
 }
 
-template <int N, typename T>
-__global__ void __launch_bounds__(nthreads<N>(), apply2_min_blocks<N, T>())
+template <int N, typename T, int V>
+__global__ void __launch_bounds__(nthreads<N>(), (apply2_min_blocks<N, T, V>()))
 apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   apply2_body<N, T>(m, e0 + blockIdx.x, u, y, partial ? partial + blockIdx.x : nullptr, smem_raw);
 }
 
 // a batch of meshes: CTA b works on element work[b].y of instance work[b].x
-template <int N, typename T>
-__global__ void __launch_bounds__(nthreads<N>(), apply2_min_blocks<N, T>())
+template <int N, typename T, int V>
+__global__ void __launch_bounds__(nthreads<N>(), (apply2_min_blocks<N, T, V>()))
 apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work,
                     const long long *__restrict__ dof_off, const T *__restrict__ u, T *__restrict__ y,
                     double *__restrict__ partial) {
@@ -886,37 +891,86 @@ apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__
   apply2_body<N, T>(sm, w.y, u + off, y + off, partial ? partial + blockIdx.x : nullptr, smem_raw);
 }
 
-template <int N, typename T>
-cudaError_t launch_apply2_batch(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
-                                const T *u, T *y, double *partial, cudaStream_t st) {
-  constexpr size_t sm = apply2_smem<N, T>();
-  static int configured_device = -1;
+// the dynamic shared-memory opt-in of a kernel, once per device
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes, int &configured_device) {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t err = cudaFuncSetAttribute(apply2_batch_kernel<N, T>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    configured_device = dev;
-  }
+  if (configured_device == dev) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (err == cudaSuccess) configured_device = dev;
+  return err;
+}
+
+template <int N, typename T, int V>
+cudaError_t launch_apply2_batch_v(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
+                                  const T *u, T *y, double *partial, cudaStream_t st) {
+  constexpr size_t sm = apply2_smem<N, T>();
+  static int configured_device = -1;
+  cudaError_t err = allow_smem(apply2_batch_kernel<N, T, V>, sm, configured_device);
+  if (err != cudaSuccess) return err;
   if (nwork <= 0) return cudaSuccess;
-  apply2_batch_kernel<N, T><<<nwork, nthreads<N>(), sm, st>>>(meshes, work, dof_off, u, y, partial);
+  apply2_batch_kernel<N, T, V><<<nwork, nthreads<N>(), sm, st>>>(meshes, work, dof_off, u, y, partial);
   return cudaGetLastError();
 }
 
-template <int N, typename T>
-cudaError_t launch_apply2(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+template <int N, typename T, int V>
+cudaError_t launch_apply2_v(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
   constexpr size_t sm = apply2_smem<N, T>();
   static int configured_device = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t err = cudaFuncSetAttribute(apply2_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    configured_device = dev;
-  }
-  apply2_kernel<N, T><<<m.E, nthreads<N>(), sm, st>>>(m, 0, u, y, partial);
+  cudaError_t err = allow_smem(apply2_kernel<N, T, V>, sm, configured_device);
+  if (err != cudaSuccess) return err;
+  apply2_kernel<N, T, V><<<m.E, nthreads<N>(), sm, st>>>(m, 0, u, y, partial);
   return cudaGetLastError();
+}
+
+// variant 1 exists for FP32 only
+template <int N, typename T>
+cudaError_t launch_apply2_batch(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
+                                const T *u, T *y, double *partial, cudaStream_t st, int var) {
+  if constexpr (sizeof(T) == 4) {
+    if (var == 1) return launch_apply2_batch_v<N, T, 1>(meshes, work, nwork, dof_off, u, y, partial, st);
+  }
+  return launch_apply2_batch_v<N, T, 0>(meshes, work, nwork, dof_off, u, y, partial, st);
+}
+
+template <int N, typename T>
+cudaError_t launch_apply2(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var) {
+  if constexpr (sizeof(T) == 4) {
+    if (var == 1) return launch_apply2_v<N, T, 1>(m, u, y, partial, st);
+  }
+  return launch_apply2_v<N, T, 0>(m, u, y, partial, st);
+}
+
+// time per launch (us) of both FP32 variants on one mesh (m1) or one degree
+// group of a batch: 3 untimed launches, then 10 between CUDA events on st
+template <int N>
+cudaError_t tune_apply2(const DevMesh *m1, const DevMesh *meshes, const int2 *work, int nwork,
+                        const long long *dof_off, const float *u, float *y, cudaStream_t st, float us[2]) {
+  cudaEvent_t ev[2];
+  cudaError_t err = cudaEventCreate(&ev[0]);
+  if (err != cudaSuccess) return err;
+  err = cudaEventCreate(&ev[1]);
+  if (err != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return err;
+  }
+  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+    for (int i = 0; i < 13 && err == cudaSuccess; ++i) {
+      if (i == 3) err = cudaEventRecord(ev[0], st);
+      if (err != cudaSuccess) break;
+      err = m1 ? launch_apply2<N, float>(*m1, u, y, nullptr, st, v)
+               : launch_apply2_batch<N, float>(meshes, work, nwork, dof_off, u, y, nullptr, st, v);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev[1], st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(ev[1]);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    us[v] = ms * 100.0f;  // 10 launches: ms / 10 * 1000
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return err;
 }
 
 template <int N, typename T, typename TIO>
@@ -938,21 +992,16 @@ cudaError_t launch_apply_range(const DevMesh &m, int s0, int s1, const TIO *u, T
   return cudaGetLastError();
 }
 
-template <int N, typename T>
-cudaError_t launch_apply_n(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
-  return launch_apply2<N, T>(m, u, y, partial, st);
-}
-
 template <typename T>
-cudaError_t launch_apply_t(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+cudaError_t launch_apply_t(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var) {
   switch (m.N) {
-    case 3: return launch_apply_n<3, T>(m, u, y, partial, st);
-    case 4: return launch_apply_n<4, T>(m, u, y, partial, st);
-    case 5: return launch_apply_n<5, T>(m, u, y, partial, st);
-    case 6: return launch_apply_n<6, T>(m, u, y, partial, st);
-    case 7: return launch_apply_n<7, T>(m, u, y, partial, st);
-    case 8: return launch_apply_n<8, T>(m, u, y, partial, st);
-    case 9: return launch_apply_n<9, T>(m, u, y, partial, st);
+    case 3: return launch_apply2<3, T>(m, u, y, partial, st, var);
+    case 4: return launch_apply2<4, T>(m, u, y, partial, st, var);
+    case 5: return launch_apply2<5, T>(m, u, y, partial, st, var);
+    case 6: return launch_apply2<6, T>(m, u, y, partial, st, var);
+    case 7: return launch_apply2<7, T>(m, u, y, partial, st, var);
+    case 8: return launch_apply2<8, T>(m, u, y, partial, st, var);
+    case 9: return launch_apply2<9, T>(m, u, y, partial, st, var);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1334,11 +1383,24 @@ cudaError_t launch_energy_dual_n(const DevMesh &m, int s0, int s1, const double 
 }  // namespace
 
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
-                            double *partial, const void *dotwith, cudaStream_t st) {
-  (void)dotwith;
+                            double *partial, int var, cudaStream_t st) {
   if (precision == TN_F64)
-    return launch_apply_t<double>(m, (const double *)u, (double *)y, partial, st);
-  return launch_apply_t<float>(m, (const float *)u, (float *)y, partial, st);
+    return launch_apply_t<double>(m, (const double *)u, (double *)y, partial, st, 0);
+  return launch_apply_t<float>(m, (const float *)u, (float *)y, partial, st, var);
+}
+
+cudaError_t tn_tune_apply(const DevMesh *m1, int N, const DevMesh *meshes, const int2 *work, int nwork,
+                          const long long *dof_off, const float *u, float *y, cudaStream_t st, float us[2]) {
+  switch (N) {
+    case 3: return tune_apply2<3>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 4: return tune_apply2<4>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 5: return tune_apply2<5>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 6: return tune_apply2<6>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 7: return tune_apply2<7>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 8: return tune_apply2<8>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    case 9: return tune_apply2<9>(m1, meshes, work, nwork, dof_off, u, y, st, us);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st) {
@@ -1404,15 +1466,15 @@ cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const doub
 
 cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
                                   const long long *dof_off, const void *u, void *y, double *partial,
-                                  cudaStream_t st) {
+                                  int var, cudaStream_t st) {
   switch (N) {
 #define TN_CASE(NN)                                                                                    \
   case NN:                                                                                            \
     return precision == TN_F64                                                                        \
                ? launch_apply2_batch<NN, double>(meshes, work, nwork, dof_off, (const double *)u,    \
-                                                 (double *)y, partial, st)                            \
+                                                 (double *)y, partial, st, 0)                         \
                : launch_apply2_batch<NN, float>(meshes, work, nwork, dof_off, (const float *)u,      \
-                                                (float *)y, partial, st);
+                                                (float *)y, partial, st, var);
     TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
     default: return cudaErrorInvalidValue;

@@ -596,10 +596,10 @@ int reduction_blocks() { return kRedBlocks; }
 }  // namespace tn
 
 cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const {
-  if (m) return tn_launch_apply(*m, prec, u, y, part, nullptr, st);
+  if (m) return tn_launch_apply(*m, prec, u, y, part, mvar, st);
   for (int g = 0; g < ngroups; ++g) {
     cudaError_t e = tn_launch_apply_batch(gN[g], prec, meshes, gwork[g], gcount[g], dof_off, u, y,
-                                          part ? part + gpart_off[g] : nullptr, st);
+                                          part ? part + gpart_off[g] : nullptr, gvar[g], st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -117,14 +117,19 @@ cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const dou
 // part[b] = partial sums of lam . db/dr0 (beam width derivative of the load)
 cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const double *lam, double *part,
                               int nparts, cudaStream_t st);
-// batches: one launch per polynomial degree; work[b] = (instance, element)
+// batches: one launch per polynomial degree; work[b] = (instance, element).
+// var: occupancy variant of the FP32 kernel (0 or 1, same results)
 cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
                                   const long long *dof_off, const void *u, void *y, double *partial,
-                                  cudaStream_t st);
+                                  int var, cudaStream_t st);
+// us[v]: time per launch of FP32 variant v on one mesh (m1) or on one degree
+// group of a batch (m1 = nullptr); y is overwritten
+cudaError_t tn_tune_apply(const DevMesh *m1, int N, const DevMesh *meshes, const int2 *work, int nwork,
+                          const long long *dof_off, const float *u, float *y, cudaStream_t st, float us[2]);
 cudaError_t tn_launch_energy_batch(int N, const DevMesh *meshes, const int2 *work, int nwork,
                                    const long long *dof_off, const double *u, double *out, cudaStream_t st);
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
-                            double *partial, const void *dotwith, cudaStream_t st);
+                            double *partial, int var, cudaStream_t st);
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st);
 cudaError_t tn_launch_diag(const DevMesh &m, double *d, cudaStream_t st);
 cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem_energy,

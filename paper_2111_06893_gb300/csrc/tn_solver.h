@@ -28,6 +28,8 @@ struct OpSys {
   int glines[8] = {0};
   int grz_off[8] = {0};
   const long long *dof_off = nullptr, *fac_off = nullptr;
+  int mvar = 0;           // occupancy variant of the FP32 operator kernel (single mesh)
+  int gvar[8] = {0};      // the same per degree group of a batch
   int n_apply_parts = 0;  // partial sums written by one apply
   int n_rz_parts = 0;     // partial sums of r.z written by one z-line solve (r.r: as many, after them)
   int *zerr = nullptr;    // set to 1 by a z-line solve whose staging wait ran out

@@ -29,7 +29,8 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
-           "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes"]
+           "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes",
+           "tn_apply_tuning", "tn_set_apply_variant"]
 
 
 class MeshDesc(C.Structure):
@@ -252,6 +253,20 @@ class Context:
         self._check_tensor(y, u.dtype, "y")
         _check(load().tn_apply_operator(self._h, prec, C.c_void_p(u.data_ptr()), C.c_void_p(y.data_ptr())))
         return y
+
+    def apply_tuning(self):
+        """{degree: {"variant": 0 | 1, "us": [variant 0, variant 1]}} for the
+        degrees whose FP32 operator variant is settled (timed by the first
+        FP32 apply or mixed solve, or fixed by set_apply_variant)."""
+        var = (C.c_int * 7)()
+        us = (C.c_double * 14)()
+        _check(load().tn_apply_tuning(self._h, var, us))
+        return {p: {"variant": var[p - 2], "us": [us[2 * (p - 2)], us[2 * (p - 2) + 1]]}
+                for p in range(2, 9) if var[p - 2] >= 0}
+
+    def set_apply_variant(self, degree, variant):
+        """Fix the FP32 operator variant (0 or 1) of one degree; -1: time it again."""
+        _check(load().tn_set_apply_variant(self._h, int(degree), int(variant)))
 
     def rhs(self, out=None):
         out = self._vec(self._torch.float64) if out is None else out

@@ -65,3 +65,9 @@ def test_null_arguments_rejected(lib):
     assert lib.tn_apply_operator(None, 0, None, None) == -1
     assert lib.tn_solve(None, None, None, None) == -1
     lib.tn_destroy(None)
+
+
+def test_apply_tuning_entry_points_reject_null_context(lib):
+    var = (C.c_int * 7)()
+    assert lib.tn_apply_tuning(None, var, None) != 0
+    assert lib.tn_set_apply_variant(None, 6, 0) != 0
