@@ -64,9 +64,11 @@ ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, one launc
                  (43236096 + 512 + 2476544 + 0 + 131932160 + 996608 + 102644224 + 581376) * 1.0}
 
 
-# DRAM bytes (read + write) of one FP32 apply, from `ncu --set full -k
-# regex:apply2_kernel` of `bench.py --mode apply --workload single_coating`
-APPLY_TRAFFIC = {("single_coating", "apply2_kernel<7,float>"): 8144128.0}
+# DRAM bytes (read + write) of one FP32 apply per occupancy variant, from
+# `ncu --set full -k regex:apply2_kernel` of `bench.py --mode apply --workload
+# single_coating` (variant 1: its register spills add local-memory traffic)
+APPLY_TRAFFIC = {("single_coating", "apply2_kernel<7,float,0>"): 8144128.0,
+                 ("single_coating", "apply2_kernel<7,float,1>"): 10237184.0 + 704768.0}
 
 
 def measured_peaks():
@@ -408,6 +410,8 @@ def main():
 
     t32 = time_apply(x32, y32, 200)
     tuning = ctx.apply_tuning()  # FP32 operator variant per degree, timed by the first FP32 call
+    akernel = ("apply2_batch_kernel<N,float,V>" if batched
+               else f"apply2_kernel<{N},float,{tuning.get(N - 1, {}).get('variant', 0)}>")
     t64 = time_apply(x64, y64, 20)
 
     # the dominant kernel of the step: the FP32 preconditioner solve (column lines)
@@ -544,8 +548,8 @@ def main():
                      "peak_source": peak_src},
         "roofline_apply": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                            "frac": achieved / peak_fp32,
-                           "traffic": None if batched else APPLY_TRAFFIC.get((args.workload, f"apply2_kernel<{N},float>")),
-                           "kernel": "apply2_batch_kernel<N,float>" if batched else f"apply2_kernel<{N},float>",
+                           "traffic": None if batched else APPLY_TRAFFIC.get((args.workload, akernel)),
+                           "kernel": akernel,
                            "flops_per_dof": flops_dof,
                            "hbm_GBps_algorithmic": 8 * ndof / t32 / 1e9,
                            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
