@@ -16,7 +16,9 @@
 // and its logical normal derivative are gathered (neighbour data are L2
 // hits), then the neighbour traction is formed at the face nodes, then every
 // node forms its strain, stress, face terms and fluxes, and finally the
-// transposed derivative contractions give y.
+// transposed derivative contractions give y.  The FP32 kernel is built in two
+// occupancy variants (registers per thread against CTAs per SM) with
+// identical arithmetic; tn_tune_apply times both on the mesh at hand.
 #include <cstdio>
 #include <type_traits>
 
