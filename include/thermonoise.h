@@ -145,7 +145,9 @@ tn_status tn_apply_operator(tn_ctx *ctx, int precision, const void *u_dev, void 
  * microseconds of variants 0 and 1 for each degree (0 where not timed).
  * tn_set_apply_variant fixes the variant of one degree (0 or 1; the
  * autotuner then leaves it alone) or, with -1, lets it be timed again.
- * Building a mesh or batch resets both. */
+ * Building a mesh or batch resets both.  variant and us are caller-owned host
+ * arrays; neither call touches the GPU.  TN_EINVAL for a null context or
+ * variant array, a degree outside 2..8 or a variant outside -1..1. */
 tn_status tn_apply_tuning(const tn_ctx *ctx, int *variant, double *us);
 tn_status tn_set_apply_variant(tn_ctx *ctx, int degree, int variant);
 
