@@ -13,6 +13,9 @@
 * ``half_space_energy``: closed-form energy of an isotropic half-space under
   the pressure profile of Eq. (laserbeam), (1 - nu^2) F0^2 / (2 sqrt(2 pi) Y r0),
   and the same number by quadrature of the Boussinesq surface response.
+* ``thin_coating_energy``: the coating's energy to first order in its
+  thickness on an isotropic half-space (the limit behind the approximate
+  noise formula Eq. (approx_analytic)), from the substrate's surface strain.
 
 Test infrastructure: slow, plain FP64, imported only by tests and by the
 CPU-baseline leg of the benchmark.
@@ -22,6 +25,8 @@ import math
 import numpy as np
 import scipy.sparse.linalg as spla
 from scipy import integrate, special
+
+from .materials import lame_from_young
 
 BOLTZMANN = 1.380649e-23
 
@@ -71,6 +76,31 @@ def half_space_energy_quadrature(Y, nu, F0, r0):
 
     val, _ = integrate.quad(lambda k: p_hat(k) ** 2, 0.0, 16.0 / r0, limit=200)
     return (1.0 - nu ** 2) / (2.0 * math.pi * Y) * val
+
+
+def thin_coating_energy(Yc, nuc, Ys, nus, d, F0, r0):
+    """Energy of an isotropic coating (Yc, nuc) of thickness d << r0 on an
+    isotropic half-space (Ys, nus) loaded by the beam pressure p(r) of
+    Eq. (laserbeam), to first order in d.
+
+    A thin coating follows the substrate's in-plane surface strain
+    (continuous displacement) and carries the normal traction -p and no
+    shear traction.  On a half-space a normal surface load moves the
+    surface sideways by the gradient of a potential whose in-plane
+    Laplacian is -(1 - 2 nus)(1 + nus) p / Ys (Boussinesq's point load gives
+    the inward surface displacement (1 - 2 nu)(1 + nu) P / (2 pi Y r);
+    loads superpose), so the in-plane strain trace there is e = -a p with
+    a = (1 - 2 nus)(1 + nus) / Ys, and for a gradient field the integral of
+    eps_ab eps_ab over the surface equals that of e^2.  The coating's Hooke
+    law with sigma_zz = -p fixes eps_zz = -(1 - lam_c a) p / (lam_c + 2 mu_c),
+    every term of the energy density is then a multiple of p^2, and
+    int p^2 dA = F0^2 / (2 pi r0^2)."""
+    lam, mu = lame_from_young(Yc, nuc)
+    a = (1.0 - 2.0 * nus) * (1.0 + nus) / Ys
+    e = -a                                  # in-plane strain trace per unit p
+    ezz = -(1.0 - lam * a) / (lam + 2.0 * mu)  # normal strain per unit p
+    two_w = lam * (e + ezz) * e + 2.0 * mu * e * e - ezz  # sigma : eps per unit p^2
+    return 0.5 * d * two_w * F0 ** 2 / (2.0 * math.pi * r0 ** 2)
 
 
 def solve_cg(op, A, b, rtol=1e-12, maxiter=20000):

@@ -360,6 +360,25 @@ def test_noise_psd_independent_of_force_and_levin_half_space():
     assert abs(Sq / levin - 1) < 1e-13
 
 
+def test_thin_coating_energy_and_psd_reproduce_the_approximate_formula():
+    """Eq. (approx_analytic): the paper's thin-coating noise for amorphous
+    layers on a half-space (beam width w = sqrt(2) r0, one coating loss
+    angle).  The oracle's route to the same number is independent of it: the
+    coating energy from the substrate's surface strain, then the PSD
+    constant of the fluctuation-dissipation reading.  Agreement for unlike
+    materials pins both the energy derivation and the constant 4/pi."""
+    kT, f, d, r0, phi = 300 * ob.BOLTZMANN, 100.0, 3e-3, 1.3, 4e-4
+    for Yc, nuc, Ys, nus in ((140e9, 0.23, 72e9, 0.17), (72e9, 0.17, 72e9, 0.17),
+                             (100e9, 0.32, 72e9, 0.17), (60e9, 0.0, 200e9, 0.35)):
+        for F0 in (1.0, 2.5):
+            U = ob.thin_coating_energy(Yc, nuc, Ys, nus, d, F0, r0)
+            S = ob.noise_psd([U], [phi], kT, f, F0)
+            paper = (kT / (math.pi ** 2 * f) * (1 - nus ** 2) / (r0 * Ys) * d / r0
+                     * phi / (Ys * Yc * (1 - nuc ** 2) * (1 - nus ** 2))
+                     * (Yc ** 2 * (1 + nus) ** 2 * (1 - 2 * nus) ** 2 + Ys ** 2 * (1 + nuc) ** 2 * (1 - 2 * nuc)))
+            assert abs(S / paper - 1) < 1e-13, (Yc, nuc, Ys, nus, S / paper)
+
+
 def test_split_jacobian_matches_full_complex_step():
     """The geometry's Jacobian (complex step of the cross-section map, closed
     form dZ/dzeta) equals the full 3-D complex-step Jacobian of the map."""
