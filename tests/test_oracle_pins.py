@@ -379,6 +379,24 @@ def test_thin_coating_energy_and_psd_reproduce_the_approximate_formula():
             assert abs(S / paper - 1) < 1e-13, (Yc, nuc, Ys, nus, S / paper)
 
 
+def test_layer_energy_sum_approaches_half_b_dot_u_with_degree():
+    """Sec. 2.1 energy, read as the element's own unlifted strain energy:
+    its layer sum differs from the discrete energy 1/2 b.u by the jump and
+    penalty terms, a gap that must vanish as the degree grows (a wrong
+    factor or a lifted/unlifted mix-up in the density would leave it)."""
+    gaps = []
+    for p in (2, 3, 4, 5):
+        d = W.box([-2.0, 0.0, 2.0], [-2.0, 0.0, 2.0], [0.0, -1.0, -2.5], p, W.FUSED_SILICA,
+                  penalty_C=3.0, bc_side="fixed", bc_bottom="fixed", r0=0.8)
+        op = Operator(Mesh(d))
+        b = op.rhs()
+        u = ob.solve(op.assemble(), b)
+        E = 0.5 * float(b @ u)
+        gaps.append(abs(ob.layer_energies(op, u).sum() - E) / E)
+    assert all(g1 < g0 for g0, g1 in zip(gaps, gaps[1:])), gaps
+    assert gaps[0] > 1e-3 and gaps[-1] < 1e-4, gaps
+
+
 def test_split_jacobian_matches_full_complex_step():
     """The geometry's Jacobian (complex step of the cross-section map, closed
     form dZ/dzeta) equals the full 3-D complex-step Jacobian of the map."""
