@@ -122,6 +122,24 @@ class Operator:
         p = self.mesh.p
         return self.C * (p + 1) ** 2 / h
 
+    @staticmethod
+    def h_min(h1, h2):
+        """min(h_int, h_ext) of Eq. (penalty), node by node.  For real h it
+        is the minimum.  Under a complex step (derivatives) two sides whose
+        real parts agree to 1e-12 relative count as a tie (equal layer
+        thicknesses meet there, computed from slab positions with rounding):
+        the value is the smaller real part and the derivative the smaller of
+        the two, i.e. the derivative for an increasing parameter, which is
+        the same seen from both elements of the face."""
+        if not (np.iscomplexobj(h1) or np.iscomplexobj(h2)):
+            return np.minimum(h1, h2)
+        h1 = np.asarray(h1, dtype=complex)
+        h2 = np.asarray(h2, dtype=complex)
+        r1, r2 = h1.real, h2.real
+        tie = np.abs(r1 - r2) <= 1e-12 * np.maximum(np.abs(r1), np.abs(r2))
+        tied = np.minimum(r1, r2) + 1j * np.minimum(h1.imag, h2.imag)
+        return np.where(tie, tied, np.where(r1 < r2, h1, h2))
+
     # ---------------------------------------------------------- the rows
     def element_rows(self, e):
         """Blocks {e2: A[e-rows, e2-cols]} of the weak-form operator."""
@@ -145,7 +163,7 @@ class Operator:
             perm = mesh.face_perm(e, f)
             F2 = mesh.face_nodes(f2)[perm]
             h2 = mesh.face_geometry(e2, f2)["h"][perm]
-            sig = self.sigma(np.minimum(fg["h"], h2))
+            sig = self.sigma(self.h_min(fg["h"], h2))
             Ystar = 0.5 * (self.Ye(e) + self.Ye(e2))
             Pen = self.penalty_op(nvec, Ystar, sig)
             V2 = self.value_op(F2)
@@ -254,7 +272,7 @@ class Operator:
                     jump = ue[:, F].T - u2[:, F2].T
                     nu_star_minus = -0.5 * jump  # {u} - u_int
                     h2 = mesh.face_geometry(e2, f2)["h"][perm]
-                    sig = self.sigma(np.minimum(fg["h"], h2))
+                    sig = self.sigma(self.h_min(fg["h"], h2))
                     Ystar = 0.5 * (Y + Y2)
                     tr_ext = np.einsum("qa,ajbl,qbl->qj", nvec, Y2, grad2)
                     pen = sig[:, None] * np.einsum("qa,ajbl,qb,ql->qj", nvec, Ystar, nvec, jump)

@@ -25,11 +25,21 @@ from . import observables as ob
 H = 1e-30
 
 
-def energies(desc, dense=True):
+def energies(desc, solver="refined"):
+    """Layer energies of the mirror `desc` (complex-valued under a complex
+    step).  solver: "refined" (iterative refinement with extended-precision
+    residuals, accurate well below FP64 rounding of a plain solve even for
+    thin layers), "dense" (dense Cholesky / LU) or "lu" (sparse LU)."""
     op = Operator(Mesh(desc))
     A = op.assemble()
     b = op.rhs()
-    u = ob.solve_dense(A, b) if dense else ob.solve(A, b)
+    if solver == "refined":
+        u = ob.solve_refined(A, b)
+        u = u.astype(np.complex128 if np.iscomplexobj(u) else np.float64)
+    elif solver == "dense":
+        u = ob.solve_dense(A, b)
+    else:
+        u = ob.solve(A, b)
     return ob.layer_energies(op, u)
 
 
@@ -51,7 +61,7 @@ def perturbed(desc, param, step):
     return d
 
 
-def energy_derivative(desc, param, dense=True):
+def energy_derivative(desc, param, solver="refined"):
     """dU_i / d param for every layer i (complex step)."""
-    U = energies(perturbed(desc, param, 1j * H), dense=dense)
+    U = energies(perturbed(desc, param, 1j * H), solver=solver)
     return np.imag(U) / H

@@ -126,3 +126,36 @@ def solve_dense(A, b):
         return sl.lu_solve(sl.lu_factor(A.toarray(), check_finite=False), b)
     c = sl.cho_factor(A.toarray(), lower=True, overwrite_a=True, check_finite=False)
     return sl.cho_solve(c, b)
+
+
+def solve_refined(A, b, max_steps=12, info=None):
+    """A u = b for the FP64 matrix A to well below FP64 rounding of a plain
+    factorisation: classical iterative refinement (Wilkinson), x += A^-1 r
+    with the residual r = b - A x formed in extended precision
+    (np.longdouble: 64-bit significand on x86, IEEE quad on Arm) and the
+    correction from one sparse LU of A in FP64.  Each step shrinks the error
+    by about cond(A) eps64; it stops once a correction no longer shrinks.
+    Thin coating layers give cond(A) ~ 1e8, where a plain FP64 solve keeps
+    ~1e-9 relative error in the energies; this solve is the reference the
+    GPU results are graded against there.  Complex systems (complex-step
+    derivatives) are refined the same way in complex extended precision.
+    Returns the solution in extended precision; info (a dict) receives the
+    relative size of every correction."""
+    cplx = np.iscomplexobj(A.data) or np.iscomplexobj(b)
+    ext = np.clongdouble if cplx else np.longdouble
+    work = np.complex128 if cplx else np.float64
+    lu = spla.splu(A.tocsc().astype(work))
+    Ae = A.tocsr().astype(ext)
+    be = np.asarray(b).astype(ext)
+    x = lu.solve(np.asarray(b, dtype=work)).astype(ext)
+    steps = []
+    for _ in range(max_steps):
+        r = be - Ae @ x
+        d = lu.solve(r.astype(work))
+        x = x + d.astype(ext)
+        steps.append(float(np.max(np.abs(d)) / np.max(np.abs(x))))
+        if steps[-1] < 1e-17 or (len(steps) >= 3 and steps[-1] > 0.5 * steps[-3]):
+            break
+    if info is not None:
+        info["corrections"] = steps
+    return x

@@ -419,3 +419,55 @@ def test_complex_step_energy_gradients_match_central_differences():
         cs = G.energy_derivative(d, p)
         fd = np.real(G.energies(G.perturbed(d, p, h)) - G.energies(G.perturbed(d, p, -h))) / (2 * h)
         assert np.max(np.abs(cs - fd)) <= tol * np.max(np.abs(cs)), (p, cs, fd)
+
+
+# ------------------------------------------------ refined solve, tie rule
+
+def test_refined_solve_recovers_exact_integer_solution():
+    """solve_refined on Pascal matrices (integer, SPD, cond 4e9 and 2e7) with
+    integer solutions: the refined solution is exact to well below what a
+    plain FP64 factorisation reaches; under a complex step the imaginary
+    part (a derivative) is recovered too."""
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+    rng = np.random.default_rng(0)
+    A = sl.pascal(10).astype(float)
+    x = rng.integers(-3, 4, size=10).astype(float)
+    b = A @ x
+    plain = np.linalg.solve(A, b)
+    xr = ob.solve_refined(sp.csr_matrix(A), b)
+    assert np.max(np.abs(plain - x)) > 1e-9  # the plain solve is visibly off
+    assert np.max(np.abs(np.asarray(xr, dtype=float) - x)) < 1e-10
+    A = sl.pascal(8).astype(float)
+    x = rng.integers(-3, 4, size=8).astype(float)
+    y = rng.integers(-3, 4, size=8).astype(float)
+    B = sl.toeplitz(np.arange(8) % 5).astype(float)
+    h = 1e-30
+    xc = ob.solve_refined(sp.csr_matrix(A + 1j * h * B), A @ x + 1j * h * (B @ x + A @ y))
+    assert np.max(np.abs(np.real(xc).astype(float) - x)) < 1e-12
+    assert np.max(np.abs(np.imag(xc).astype(float) / h - y)) < 2e-9
+
+
+@pytest.mark.parametrize("dz_bottom", [0.0, -1e-14])
+def test_tie_of_face_sizes_takes_the_forward_derivative(dz_bottom):
+    """Two slabs of equal thickness (exactly, or within rounding): the
+    complex-step derivative in the shared boundary equals the forward
+    difference (derivative for an increasing parameter), not the backward
+    one, which differs because min(h_int, h_ext) has a kink there."""
+    from oracle import gradient as G
+    desc = W.box([-1.0, 1.0], [-1.0, 1.0], [0.0, -0.5, -1.0 + dz_bottom], 2, W.FUSED_SILICA,
+                 penalty_C=3.0, bc_side="fixed", bc_bottom="fixed", r0=0.7)
+    cs = G.energy_derivative(desc, ("slab_z", 1))[0]
+
+    def U(dz):
+        d = dict(desc)
+        z = list(desc["slab_z"])
+        z[1] += dz
+        d["slab_z"] = z
+        return G.energies(d)[0]
+
+    U0, h = U(0.0), 1e-5
+    fwd = 2 * (U(h / 2) - U0) / (h / 2) - (U(h) - U0) / h
+    bwd = 2 * (U0 - U(-h / 2)) / (h / 2) - (U0 - U(-h)) / h
+    assert abs(cs - fwd) < 1e-6 * abs(fwd), (cs, fwd)
+    assert abs(bwd - fwd) > 1e-3 * abs(fwd), (bwd, fwd)
