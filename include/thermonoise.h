@@ -118,6 +118,15 @@ typedef struct {
 } tn_material;
 tn_status tn_set_materials(tn_ctx *ctx, int n, const tn_material *m);
 
+/* The stiffness entries an isotropic material gets in tn_set_materials and
+ * in the gradients of tn_energy_grad: c_host[3] = (c11, c12, c44) =
+ * (lambda + 2 mu, lambda, mu) from Young's modulus Y and Poisson ratio nu
+ * (the footnote to Eq. (constrel_iso), inverted), and, if dc_host is not
+ * NULL, dc_host[2 q + 0] = d c_q / dY, dc_host[2 q + 1] = d c_q / dnu, so that
+ * dJ/dY = sum_q dJ/dc_q dc_host[2 q].  Host only; TN_EINVAL unless Y > 0 and
+ * -1 < nu < 1/2. */
+tn_status tn_iso_moduli(double Y, double nu, double *c_host, double *dc_host);
+
 /* Gaussian beam p(r) = F0 exp(-r^2/r0^2) / (pi r0^2) (Eq. (laserbeam)),
  * centred on the z axis. r0 > 0. */
 tn_status tn_set_beam(tn_ctx *ctx, double r0, double F0);
@@ -178,6 +187,9 @@ tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
  * (caller-owned device buffers of tn_ndof() values, 16-byte aligned, not
  * overlapping). */
 tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *r_dev, void *z_dev);
+/* (tn_precond_apply is asynchronous: its staging waits use the 1 s default
+ * of tn_solve_opts.device_wait_limit_s, and a wait that ran out leaves z
+ * incomplete without an error code; tn_solve reports timeouts.) */
 
 /* Bytes of FP32 factors one FP32 application of `precond` reads (building
  * the factors first if needed; TN_PC_JACOBI: the inverse diagonal), for
@@ -214,6 +226,14 @@ typedef struct {
                                changes by <= energy_rtol (relative) between
                                two checks (refinement steps, or check_every
                                FP64 iterations); 0: residual test only     */
+  double device_wait_limit_s; /* bound on every device-side wait of the line
+                               solves (a staged factor copy landing in shared
+                               memory), in seconds of the GPU's global timer;
+                               0: 1 s.  A wait that runs out ends its kernel
+                               (after a bounded wait for its copies still in
+                               flight), the solve stops at the next check and
+                               returns TN_ETIMEOUT, which outranks every other
+                               outcome; the context stays usable.  [0, 3600] */
 } tn_solve_opts;
 typedef struct {
   int status;
@@ -300,6 +320,15 @@ tn_status tn_batch_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const dou
  * no clearing is needed.  u_dev: FP64 field; U_host: n_layers doubles.
  * Synchronises the context's stream. */
 tn_status tn_layer_energies_noalloc(tn_ctx *ctx, const double *u_dev, double *U_host);
+
+/* Measured fused-multiply-add peak of the CUDA cores of `device` in
+ * precision TN_F32 or TN_F64 (flop/s, an FMA counted as 2): the roofline
+ * denominator of the operator apply, which is bound by arithmetic, not HBM
+ * (no counterpart in the paper).  Independent FMA chains in registers on
+ * 4 CTAs of 512 threads per SM, CUDA events around 5 launches after a
+ * warm-up, at whatever clocks the GPU runs (none are set).  Takes ~0.1 s.
+ * *flops_per_s: host.  TN_EINVAL for a bad device or precision. */
+tn_status tn_fma_peak(int device, int precision, double *flops_per_s);
 
 /* Brownian noise PSD from the energies (Eq. (thermalnoise) with Eq. (wdiss)
  * per layer, dissipated power 2 pi f sum_i phi_i U_i):

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libthermonoise.so")
-SOURCES = ["kernels.cu", "precond.cu", "solver.cu", "capi.cu", "mesh.cpp"]
+SOURCES = ["kernels.cu", "precond.cu", "solver.cu", "capi.cu", "peak.cu", "mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -118,6 +118,8 @@ struct tn_ctx {
   int4 *d_glines = nullptr;
   long long *d_gfac_off = nullptr;
   int *d_ginst = nullptr;
+  int4 *d_gpacks = nullptr;
+  int *d_gqueue = nullptr;
   float *gfac = nullptr;
   double *gfac64 = nullptr;
   double *gpart = nullptr;
@@ -129,6 +131,8 @@ struct tn_ctx {
   int apply_var[10] = {0};
   bool apply_set[10] = {false};
   float apply_us[10][2] = {};
+  // bounded device waits of the line solves (limit and timeout flag)
+  TnWait *wctl = nullptr;
 };
 
 static void free_zline(tn_ctx *c) {
@@ -143,6 +147,8 @@ static void free_zgroup(tn_ctx *c) {
   dfree(c->d_glines);
   dfree(c->d_gfac_off);
   dfree(c->d_ginst);
+  dfree(c->d_gpacks);
+  dfree(c->d_gqueue);
   dfree(c->gfac);
   dfree(c->gfac64);
   dfree(c->gpart);
@@ -351,6 +357,8 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_glines, sizeof(int4) * p.ngroups);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gfac_off, sizeof(long long) * p.ngroups);
   if (e == cudaSuccess && is_batch(c)) e = cudaMalloc((void **)&c->d_ginst, sizeof(int) * p.ngroups);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gpacks, sizeof(int4) * p.packs.size());
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_gqueue, sizeof(int) * 2 * kZgMaxPk);
   if (e != cudaSuccess) {
     dfree(blk); dfree(xblk); dfree(work);
     free_zgroup(c);
@@ -374,6 +382,13 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
   for (int k = 0; k < p.ncls; ++k) {
     g.cls_N[k] = p.cls_N[k]; g.cls_G[k] = p.cls_G[k]; g.cls_start[k] = p.cls_start[k]; g.cls_n[k] = p.cls_n[k];
   }
+  g.packs = c->d_gpacks;
+  g.queue = c->d_gqueue;
+  g.npk = p.npk;
+  for (int k = 0; k < p.npk; ++k) { g.pk_N[k] = p.pk_N[k]; g.pk_start[k] = p.pk_start[k]; g.pk_n[k] = p.pk_n[k]; }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_gpacks, p.packs.data(), sizeof(int4) * p.packs.size(),
+                                            cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gqueue, 0, sizeof(int) * 2 * kZgMaxPk, st);
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_glines, p.lines.data(), sizeof(int4) * p.ngroups,
                                             cudaMemcpyHostToDevice, st);
@@ -399,7 +414,7 @@ static OpSys with_groups(OpSys s, const tn_ctx *c) {
   s.grouped = true;
   s.zg = c->zgd;
   s.n_rz_parts = c->zgd.ngroups;
-  s.zerr = c->gstatus + 1;
+  s.zerr = c->wctl;
   return s;
 }
 
@@ -493,7 +508,7 @@ static OpSys make_sys(const tn_ctx *c) {
     s.n_apply_parts = c->dm.E;
     s.n_rz_parts = tn_zline_partials(c->dm);
   }
-  s.zerr = c->zstatus ? c->zstatus + 1 : nullptr;
+  s.zerr = c->wctl;
   return s;
 }
 
@@ -569,6 +584,11 @@ tn_status tn_create(tn_ctx **out, int device, void *cuda_stream) {
   cudaError_t e = cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->wctl, sizeof(TnWait));
+  if (e == cudaSuccess) {
+    const TnWait w0{kDefaultWaitNs, 0, 0};
+    e = cudaMemcpy(c->wctl, &w0, sizeof(w0), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) {
     static LglTables tabs;
     std::memset(&tabs, 0, sizeof(tabs));
@@ -596,6 +616,7 @@ void tn_destroy(tn_ctx *c) {
   free_batch(c);
   dfree(c->d_layer_c);
   dfree(c->d_layer_c32);
+  dfree(c->wctl);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->sstream) cudaStreamDestroy(c->sstream);
@@ -673,6 +694,22 @@ tn_status tn_ndof(const tn_ctx *c, int64_t *ndof) {
   return TN_OK;
 }
 
+// (c11, c12, c44) = (lambda + 2 mu, lambda, mu) of an isotropic material and
+// their derivatives d/dY, d/dnu (footnote to Eq. (constrel_iso) inverted:
+// mu = Y / (2 (1 + nu)), lambda = Y nu / ((1 + nu)(1 - 2 nu)))
+static void iso_moduli(double Y, double nu, double c[3], double dc[6]) {
+  const double mu = Y / (2.0 * (1.0 + nu));
+  const double g = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), lam = Y * g;
+  c[0] = lam + 2.0 * mu; c[1] = lam; c[2] = mu;
+  if (!dc) return;
+  const double dmu_dY = 1.0 / (2.0 * (1.0 + nu)), dmu_dnu = -Y / (2.0 * (1.0 + nu) * (1.0 + nu));
+  const double q = (1.0 + nu) * (1.0 - 2.0 * nu);
+  const double dlam_dY = g, dlam_dnu = Y * (1.0 + 2.0 * nu * nu) / (q * q);
+  dc[0] = dlam_dY + 2.0 * dmu_dY; dc[1] = dlam_dnu + 2.0 * dmu_dnu;
+  dc[2] = dlam_dY;                dc[3] = dlam_dnu;
+  dc[4] = dmu_dY;                 dc[5] = dmu_dnu;
+}
+
 // (c11, c12, c44) per layer from the ABI materials; false + message on error
 static bool material_table(int n, const tn_material *mats, double *h, char *msg, int len) {
   for (int i = 0; i < n; ++i) {
@@ -682,9 +719,7 @@ static bool material_table(int n, const tn_material *mats, double *h, char *msg,
         std::snprintf(msg, len, "material %d: need Y > 0 and -1 < nu < 1/2", i);
         return false;
       }
-      const double mu = m.Y / (2.0 * (1.0 + m.nu));
-      const double lam = m.Y * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
-      h[3 * i] = lam + 2.0 * mu; h[3 * i + 1] = lam; h[3 * i + 2] = mu;
+      iso_moduli(m.Y, m.nu, h + 3 * i, nullptr);
     } else if (m.kind == TN_CUBIC) {
       if (!(m.c44 > 0.0) || !(m.c11 > std::fabs(m.c12)) || !(m.c11 + 2.0 * m.c12 > 0.0)) {
         std::snprintf(msg, len, "material %d: cubic stiffness not positive definite", i);
@@ -706,29 +741,10 @@ tn_status tn_set_materials(tn_ctx *c, int n, const tn_material *mats) {
   if (n != c->hm.n_layers) return fail(TN_EINVAL, "got %d materials for %d layers", n, c->hm.n_layers);
   double *h = (double *)std::malloc(sizeof(double) * 3 * n);
   if (!h) return fail(TN_ENOMEM, "host allocation failed");
-  for (int i = 0; i < n; ++i) {
-    const tn_material &m = mats[i];
-    double c11, c12, c44;
-    if (m.kind == TN_ISO) {
-      if (!(m.Y > 0.0) || !(m.nu > -1.0 && m.nu < 0.5)) {
-        std::free(h);
-        return fail(TN_EINVAL, "material %d: need Y > 0 and -1 < nu < 1/2", i);
-      }
-      const double mu = m.Y / (2.0 * (1.0 + m.nu));
-      const double lam = m.Y * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
-      c11 = lam + 2.0 * mu; c12 = lam; c44 = mu;
-    } else if (m.kind == TN_CUBIC) {
-      // positive definiteness of the cubic stiffness
-      if (!(m.c44 > 0.0) || !(m.c11 > std::fabs(m.c12)) || !(m.c11 + 2.0 * m.c12 > 0.0)) {
-        std::free(h);
-        return fail(TN_EINVAL, "material %d: cubic stiffness not positive definite", i);
-      }
-      c11 = m.c11; c12 = m.c12; c44 = m.c44;
-    } else {
-      std::free(h);
-      return fail(TN_EINVAL, "material %d: unknown kind %d", i, m.kind);
-    }
-    h[3 * i] = c11; h[3 * i + 1] = c12; h[3 * i + 2] = c44;
+  char msg[160];
+  if (!material_table(n, mats, h, msg, sizeof(msg))) {  // the same table as a batch mirror gets
+    std::free(h);
+    return fail(TN_EINVAL, "%s", msg);
   }
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   CU_TRY(cudaStreamSynchronize(c->stream), "sync before replacing materials");
@@ -1003,6 +1019,8 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return fail(TN_EINVAL, "rtol must be in (0, 1)");
   if (o->max_iter < 1) return fail(TN_EINVAL, "max_iter must be >= 1");
   if (!(o->energy_rtol >= 0.0)) return fail(TN_EINVAL, "energy_rtol must be >= 0");
+  if (!(o->device_wait_limit_s >= 0.0) || !(o->device_wait_limit_s <= 3600.0))
+    return fail(TN_EINVAL, "device_wait_limit_s must be in [0, 3600]");
   if (total_layers(c) > 65536) return fail(TN_EINVAL, "at most 65536 layers in all");
   if (o->mode == TN_SOLVE_MIXED_F32 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0) || o->max_outer < 1))
     return fail(TN_EINVAL, "mixed mode needs 0 < inner_rtol < 1 and max_outer >= 1");
@@ -1011,6 +1029,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   const int chunk = o->check_every > 0 ? o->check_every : 25;
   const auto t0 = std::chrono::steady_clock::now();
   tn::g_launches = 2;  // rhs and diagonal below
+  tn::g_timed_out = false;
   cudaStream_t s = c->sstream;
   CU_TRY(cudaEventRecord(c->ev_in, c->stream), "event");
   CU_TRY(cudaStreamWaitEvent(s, c->ev_in, 0), "event wait");
@@ -1025,17 +1044,19 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (zg) {
     tn_status zs = ensure_zgroup(c, s);
     if (zs != TN_OK) return zs;
-    CU_TRY(cudaMemsetAsync(c->gstatus + 1, 0, sizeof(int), s), "reset");
   } else if (zl) {
     tn_status zs = ensure_zline(c, s);
     if (zs != TN_OK) return zs;
-    CU_TRY(cudaMemsetAsync(c->zstatus + 1, 0, sizeof(int), s), "reset");
   }
+  // this solve's wait limit, timeout flag cleared (pageable source: copied
+  // before the call returns)
+  const TnWait wset{o->device_wait_limit_s > 0.0 ? (unsigned long long)(o->device_wait_limit_s * 1e9 + 0.5)
+                                                 : kDefaultWaitNs, 0, 0};
+  CU_TRY(cudaMemcpyAsync(c->wctl, &wset, sizeof(wset), cudaMemcpyHostToDevice, s), "wait limit");
   const OpSys sys = zg ? with_groups(make_sys(c), c) : make_sys(c);
   float *const lfac = zg ? c->gfac : c->zfac;
   double *const lfac64 = zg ? c->gfac64 : c->zfac64;
   double *const lpart = zg ? c->gpart : c->zpart;
-  int *const lstatus = zg ? c->gstatus : c->zstatus;
   tn_solve_report r{};
   tn_status result = TN_OK;
   if (bb == 0.0) {
@@ -1061,6 +1082,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       r.inner_iters += c->scal_host->iters;
       r.outer_iters += 1;
       r.applies_f64 += applies;
+      if (tn::g_timed_out) break;
       if (c->scal_host->breakdown) {
         result = fail(TN_EBREAKDOWN, "CG breakdown after %d iterations", r.inner_iters);
         break;
@@ -1130,6 +1152,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
                          c->part_red, s, &applies), "pcg f32");
       total_inner += c->scal_host->iters;
       r.applies_f32 += applies;
+      if (tn::g_timed_out) break;
       r.outer_iters += 1;
       // z = |r| d (FP64), q = A z
       CU_TRY(tn::upcast(n, c->d32, rn, c->z64, s), "upcast");
@@ -1161,7 +1184,7 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   // true FP64 residual of the returned iterate
   const bool energy_ok = r.status == 1;
   r.status = 0;
-  if (bb != 0.0 && result == TN_OK) {
+  if (bb != 0.0 && result == TN_OK && !tn::g_timed_out) {
     double rr = 0.0;
     CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
     r.applies_f64 += 1;
@@ -1170,12 +1193,16 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       result = fail(TN_ENOTCONV, "not converged: relative residual %.3e > %.3e after %d iterations",
                     r.rel_residual, o->rtol, r.inner_iters);
   }
-  int zerr = 0;
-  if (zl) CU_TRY(cudaMemcpyAsync(&zerr, lstatus + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+  TnWait wout{};
+  CU_TRY(cudaMemcpyAsync(&wout, c->wctl, sizeof(wout), cudaMemcpyDeviceToHost, s), "status");
+  const TnWait wdef{kDefaultWaitNs, 0, 0};  // later calls (tn_precond_apply) wait with the default limit
+  CU_TRY(cudaMemcpyAsync(c->wctl, &wdef, sizeof(wdef), cudaMemcpyHostToDevice, s), "wait limit");
   CU_TRY(cudaEventRecord(c->ev_out, s), "event");
   CU_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
   CU_TRY(cudaStreamSynchronize(s), "sync");
-  if (zerr && result == TN_OK) result = fail(TN_ETIMEOUT, "a z-line solve gave up waiting for its staged factors");
+  if (zl && wout.flag)  // the iterate is not trustworthy: the timeout outranks every other outcome
+    result = fail(TN_ETIMEOUT, "a line solve gave up waiting for its staged factors (limit %.3g s)",
+                  (double)wset.limit_ns * 1e-9);
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   r.status = result;
   r.launches = tn::g_launches;
@@ -1427,6 +1454,13 @@ tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   if ((st = ensure_ws(c))) return st;
   CU_TRY(energies_host(c, u, U_host, c->stream), "energies");
+  return TN_OK;
+}
+
+tn_status tn_iso_moduli(double Y, double nu, double *c, double *dc) {
+  if (!c) return fail(TN_EINVAL, "c is null");
+  if (!(Y > 0.0) || !(nu > -1.0 && nu < 0.5)) return fail(TN_EINVAL, "need Y > 0 and -1 < nu < 1/2");
+  iso_moduli(Y, nu, c, dc);
   return TN_OK;
 }
 

@@ -98,14 +98,18 @@ __device__ __forceinline__ Dual layer_coef<Dual>(const DevMesh &m, int L, int q)
   return Dual(m.layer_c[3 * L + q], m.d_layer_c ? m.d_layer_c[3 * L + q] : 0.0);
 }
 
-// min(h, h_ext) of Eq. (penalty).  At an exact tie the dual number takes the
-// smaller derivative: the one-sided derivative for an increasing parameter,
-// the same on both sides of the face (so dA/dtheta stays symmetric)
+// min(h, h_ext) of Eq. (penalty).  Sides whose h agree to 1e-12 relative
+// are a tie (equal layer thicknesses, computed from slab positions with
+// rounding): the dual number keeps the smaller value and takes the smaller
+// derivative -- the one-sided derivative for an increasing parameter, the
+// same from both elements of the face (so dA/dtheta stays symmetric)
 template <typename T>
 __device__ __forceinline__ T hmin(T a, T b) { return a < b ? a : b; }
 template <>
 __device__ __forceinline__ Dual hmin<Dual>(Dual a, Dual b) {
-  return (a.v < b.v || (a.v == b.v && a.d <= b.d)) ? a : b;
+  if (fabs(a.v - b.v) <= 1e-12 * fmax(fabs(a.v), fabs(b.v)))
+    return Dual(a.v < b.v ? a.v : b.v, a.d < b.d ? a.d : b.d);
+  return a.v < b.v ? a : b;
 }
 
 // symmetric tensors as (xx, yy, zz, xy, xz, yz)
@@ -1405,8 +1409,20 @@ cudaError_t tn_tune_apply(const DevMesh *m1, int N, const DevMesh *meshes, const
   }
 }
 
+int tn_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 152;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st) {
-  rhs_kernel<<<4 * 152, 256, 0, st>>>(m, r0, F0, b);
+  rhs_kernel<<<4 * tn_sm_count(), 256, 0, st>>>(m, r0, F0, b);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 // the lines through one cross-section point of neighbouring columns
 // together, adding the lateral-face coupling between them.
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "tn_internal.h"
@@ -333,19 +334,43 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
 }
-// wait for the phase with parity `par` of bar to complete; false after the
-// iteration limit (the copy never landed)
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned par) {
-  for (int it = 0; it < (1 << 22); ++it) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase with parity `par` of bar to complete; false once
+// limit_ns nanoseconds have passed without it (the copy never landed).
+// try_wait may suspend the thread inside the hardware until the phase
+// completes, which suits the usual limits; limits under kPollNs poll with the
+// non-blocking test_wait so that the limit itself is honoured.
+constexpr unsigned long long kPollNs = 100000ull;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned par, unsigned long long limit_ns) {
+  const bool poll = limit_ns < kPollNs;
+  unsigned long long t0 = 0;
+  for (bool first = true;; first = false) {
     unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(par)
-        : "memory");
+    if (poll)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(par)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(bar)), "r"(par)
+          : "memory");
     if (ok) return true;
+    if (first) t0 = global_ns();
+    else if (global_ns() - t0 > limit_ns) return false;
   }
-  return false;
+}
+// after a timed-out wait: the bound given to the copies still in flight
+constexpr unsigned long long kDrainNs = 2000000000ull;
+__device__ __forceinline__ unsigned long long wait_limit(const TnWait *w) {
+  return w ? w->limit_ns : kDefaultWaitNs;
 }
 
 // shared memory of one warp: two stages of one factor record, two
@@ -406,7 +431,7 @@ __device__ __forceinline__ T bcast_dot(const T *xv, Ent ent) {
 template <int N, typename T, typename F, bool UPD>
 __device__ __forceinline__ void zline_line(const DevMesh &m, const F *__restrict__ fac, T *__restrict__ r,
                                            const T *__restrict__ q, T *__restrict__ z, T alpha, int line,
-                                           int lane, unsigned char *smem, int *err, T &rz, T &rr) {
+                                           int lane, unsigned char *smem, TnWait *err, T &rz, T &rr) {
   static_assert(sizeof(T) == sizeof(F), "vectors and factors share one precision");
   constexpr int M = 3 * N, N2 = N * N, n = N * N * N;
   constexpr int LP = zlp(M), LDZ = zld(M), RS = zrec(M);
@@ -435,16 +460,21 @@ __device__ __forceinline__ void zline_line(const DevMesh &m, const F *__restrict
     }
     pend |= 1u << b;
   };
+  const unsigned long long lim = wait_limit(err);
+  // the warp agrees on the outcome; a stage counts as landed only if every
+  // lane saw it land, so that the lanes keep one view of the stages
   auto wait = [&](int b) {
-    const bool ok = mbar_wait(bar + b, (ph >> b) & 1u);
-    ph ^= 1u << b;
-    pend &= ~(1u << b);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar + b, (ph >> b) & 1u, lim));
+    if (ok) {
+      ph ^= 1u << b;
+      pend &= ~(1u << b);
+    }
     return ok;
   };
-  auto drain = [&]() {  // after a timeout: give the copies still in flight a bounded wait
-    if (pend & 1u) wait(0);
-    if (pend & 2u) wait(1);
-    if (lane == 0 && err) atomicExch(err, 1);
+  auto drain = [&]() {  // after a timeout: a bounded wait for every copy still in flight
+    if (pend & 1u) mbar_wait(bar, ph & 1u, kDrainNs);
+    if (pend & 2u) mbar_wait(bar + 1, (ph >> 1) & 1u, kDrainNs);
+    if (lane == 0 && err) atomicExch(&err->flag, 1);
   };
   if (lane == 0) {
     mbar_init(bar);
@@ -546,7 +576,7 @@ template <int N, typename T, typename F, bool UPD>
 __global__ void __launch_bounds__(128)
 zline_solve_kernel(const DevMesh m, const F *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
                    T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
-                   double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
+                   double *__restrict__ part_rr, const int *__restrict__ done, TnWait *__restrict__ err) {
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char zsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -566,7 +596,7 @@ zline_solve_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restr
                          const long long *__restrict__ fac_off, const long long *__restrict__ dof_off,
                          const F *__restrict__ fac, T *__restrict__ r, const T *__restrict__ q,
                          T *__restrict__ z, const double *__restrict__ alpha, double *__restrict__ part_rz,
-                         double *__restrict__ part_rr, const int *__restrict__ done, int *__restrict__ err) {
+                         double *__restrict__ part_rr, const int *__restrict__ done, TnWait *__restrict__ err) {
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char zsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -791,142 +821,219 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
   }
 }
 
-template <int N, int G>
-__host__ __device__ constexpr int zg_threads() { return 32 * ((G * 3 * N + 31) / 32); }
-// shared memory: two stage buffers of one record, five vectors of NT entries
-// (b, y, w / x, three reduction rows), two mbarriers
-template <int N, int G, typename T>
-constexpr size_t zg_smem() { return (2 * (size_t)zg_rec(G * 3 * N) + 6 * zg_threads<N, G>()) * sizeof(T) + 16; }
+// ---- the grouped-line solve: packed slots, one launch per degree
+// A group of G lines (3 G N rows per slab) is solved by a slot of G warps,
+// one row per thread.  A CTA of four warps takes one pack at a time from a
+// queue: one group of 4 lines, 3 + 1, 2 + 2, 2 + 1 + 1 or 1 + 1 + 1 + 1
+// lines, largest packs first.  Each slot syncs with its own named barrier
+// (a warp with __syncwarp) and streams its factor records through a ring of
+// P stages in shared memory (bulk copies completing on one mbarrier per
+// stage), so that up to P - 1 copies are in flight while one stage is used:
+// small groups, whose per-slab work is short, get the deepest rings.
+constexpr int kZgThreads = 128;  // four warps per CTA
+constexpr int kZgMaxStages = 8;
 
-// z = A_GG^{-1} r on the groups of g = G lines [gbase, gbase + gridDim.x):
-// one group per CTA, one row (unknown of a slab) per thread.
+// floats / doubles of staging per warp: two records of the largest group
+// (4 lines) across the four warps of a CTA, so that six CTAs (FP32, N = 7)
+// share an SM; smaller groups fit more stages in the same room
+template <int N, typename T>
+__host__ __device__ constexpr int zg_stage_per_warp() {
+  return pad4((zg_rec(12 * N) * 2 + 3) / 4);
+}
+template <int N, typename T>
+constexpr size_t zg_smem() {
+  return (4 * (size_t)zg_stage_per_warp<N, T>() + 4 * kZgThreads) * sizeof(T) + 4 * kZgMaxStages * 8;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+// true if p holds on any of the nthreads threads of named barrier id (and a sync)
+__device__ __forceinline__ bool named_any(int id, int nthreads, bool p) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n selp.u32 %0, 1, 0, o;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)p), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// z = A_GG^{-1} r on group grp by the slot of G warps starting at warp w0;
+// line li of the group is warp w0 + li, its rows (a, k) lanes a N + k < 3N:
 //   forward   y_s = Linv_s (r_s - O_{s-1}^T w_{s-1}),  w_s = Linv_s^T y_s
 //   backward  x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1})
-// (Z_s = Linv_{s-1} O_{s-1}); O in its factored form needs three sums over
-// each line's rows per step.  Forward stage s = record s; backward stage s =
-// Linv_s and the O factors of record s + 1; one stage in flight while the
-// other is used (bulk copies, mbarriers), the next stage's data sent to L2.
-// UPD, partial sums and the timeout flag as for single lines.
+// (Z_s = Linv_{s-1} O_{s-1}).  O in its factored form acts line by line
+// (it is block diagonal over the lines), so its products are warp shuffles
+// and warp sums; only the two triangular products cross lines, through
+// broadcast vectors in shared memory (double-buffered by step parity).
+// Stage u < S: record u; stage u >= S: Linv_s and the O factors of record
+// s + 1, s = 2S - 1 - u.  Stage u uses ring buffer u % P and mbarrier u % P
+// with phase parity (u / P) & 1.  UPD: first r <- r - alpha q (written
+// back).  Writes the group's partial r.z (= |y|^2) and r.r.  A wait that runs
+// out sets err->flag and ends the slot after bounded waits for the copies in
+// flight.
 template <int N, int G, typename T, bool UPD>
-__global__ void __launch_bounds__(zg_threads<N, G>())
-zgroup_solve_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevMesh *__restrict__ meshes,
-                    const long long *__restrict__ dof_off, const int4 *__restrict__ glines,
-                    const long long *__restrict__ gfac, int gbase, const T *__restrict__ fac, T *__restrict__ r,
-                    const T *__restrict__ q, T *__restrict__ z, const double *__restrict__ alpha,
-                    double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
-                    int *__restrict__ err) {
-  if (done && *done) return;
-  // one mesh, or a batch: the group's mirror, its mesh and its first unknown
-  int mncol = m1.ncol, mslab = m1.nslab;
-  if (ginst) {
-    const int in = ginst[gbase + blockIdx.x];
-    mncol = meshes[in].ncol;
-    mslab = meshes[in].nslab;
-    const long long o = dof_off[in];
-    r += o;
-    z += o;
-    if (UPD) q += o;
-  }
-  constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = zg_threads<N, G>();
+__device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__restrict__ r,
+                                        const T *__restrict__ q, T *__restrict__ z, const int4 *__restrict__ glines,
+                                        const long long *__restrict__ gfac, const T *__restrict__ fac, T al,
+                                        T *__restrict__ stage, int cap, T *__restrict__ vecs,
+                                        unsigned long long *__restrict__ bars, double *__restrict__ psum,
+                                        unsigned long long lim, TnWait *__restrict__ err, double *__restrict__ part_rz,
+                                        double *__restrict__ part_rr) {
+  constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = 32 * G;
   constexpr int LP = zlp(MG), RS = zg_rec(MG);
-  extern __shared__ __align__(16) unsigned char zsm[];
-  T *const buf0 = reinterpret_cast<T *>(zsm);
-  T *const vb = buf0 + 2 * RS;
-  T *const vy = vb + NT;
-  T *const vw = vy + NT;
-  T *const red = vw + NT;  // 3 x NT
-  unsigned long long *const bar = reinterpret_cast<unsigned long long *>(red + 3 * NT);
-  const int tid = threadIdx.x, grp = gbase + blockIdx.x;
-  const bool act = tid < MG;
-  const int t = act ? tid : 0;
+  const int lt = threadIdx.x - 32 * w0, bid = 1 + w0;
+  auto sync = [&]() {
+    if (G == 1) __syncwarp();
+    else named_sync(bid, NT);
+  };
+  auto any = [&](bool p) { return G == 1 ? __any_sync(0xffffffffu, p) : named_any(bid, NT, p); };
+  const int li = lt >> 5, lane = lt & 31;
+  const bool act = lane < M;
+  const int t = li * M + (act ? lane : 0);  // row of the group's blocks
+  const int a = (act ? lane : 0) / N, k = (act ? lane : 0) - a * N;
+  // broadcast vectors hold line lj's M entries at 32 lj (16-byte aligned)
+  T *const vbuf = vecs + 4 * 32 * w0;  // [2 parities][vb, vy][32 G]
+  auto vb = [&](int par) { return vbuf + par * 2 * NT; };
+  auto vy = [&](int par) { return vbuf + par * 2 * NT + NT; };
   const int4 L4 = glines[grp];
-  const int li = t / M, rem = t - li * M, a = rem / N, k = rem - a * N, lb = li * M;
   const int lid = li == 0 ? L4.x : (li == 1 ? L4.y : (li == 2 ? L4.z : L4.w));
   const int c = lid / N2, qn = lid - c * N2;
-  const size_t off = (size_t)k * N2 + qn;
-  const size_t ncol = mncol;
-  const int S = mslab;
-  auto gidx = [&](int s) { return ((size_t)(s * ncol + c) * 3 + a) * n + off; };
+  // vector entry of this row in slab s: g0 + s * gs
+  const size_t gs = (size_t)mncol * 3 * n, g0 = ((size_t)c * 3 + a) * n + (size_t)k * N2 + qn;
+  auto gidx = [&](int s) { return g0 + (size_t)s * gs; };
   const T *base = fac + gfac[grp];
-  const T al = UPD ? (T)*alpha : T(0);
   const int total = 2 * S;
-  unsigned ph = 0u, pend = 0u;
-  // stage u: forward u = s (record s); backward u = 2S - 1 - s (Linv_s, O factors of record s + 1)
-  auto stage_src = [&](int u, const T *&s0, int &n0, const T *&s1, int &n1) {
-    if (u < S) {
-      s0 = base + (size_t)u * RS;
-      n0 = RS;
-      s1 = nullptr;
-      n1 = 0;
-    } else {
-      const int s = 2 * S - 1 - u;
-      s0 = base + (size_t)s * RS;
-      n0 = LP;
-      s1 = base + (size_t)(s + 1) * RS + LP;
-      n1 = s + 1 < S ? RS - LP : 0;
-    }
-  };
-  auto issue = [&](int u) {
-    const int b = u & 1;
-    if (tid == 0) {
-      const T *s0, *s1;
-      int n0, n1;
-      stage_src(u, s0, n0, s1, n1);
+  int P = cap / RS;
+  P = P > kZgMaxStages ? kZgMaxStages : P;
+  P = P > total ? total : P;
+  // stage sources: forward stage u = record u; backward stage u (slab
+  // s = 2S - 1 - u) = Linv_s of record s and the O factors of record s + 1
+  int issued = 0, ib = 0;  // stages issued so far and the ring buffer of the next (same in every thread)
+  const T *src = base;     // lane 0: the next stage's (first) source
+  auto issue_next = [&]() {
+    if (issued >= total) return;
+    const int u = issued++, b = ib;
+    ib = ib + 1 == P ? 0 : ib + 1;
+    if (lt == 0) {
+      T *dst = stage + (size_t)b * RS;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_expect(bar + b, (unsigned)((n0 + n1) * sizeof(T)));
-      bulk_g2s(buf0 + b * RS, s0, (unsigned)(n0 * sizeof(T)), bar + b);
-      if (n1) bulk_g2s(buf0 + b * RS + LP, s1, (unsigned)(n1 * sizeof(T)), bar + b);
-      if (u + 1 < total) {  // the stage after it goes to L2 now
-        stage_src(u + 1, s0, n0, s1, n1);
-        bulk_prefetch_l2(s0, (unsigned)(n0 * sizeof(T)));
-        if (n1) bulk_prefetch_l2(s1, (unsigned)(n1 * sizeof(T)));
+      if (u < S) {
+        mbar_expect(bars + b, (unsigned)(RS * sizeof(T)));
+        bulk_g2s(dst, src, (unsigned)(RS * sizeof(T)), bars + b);
+        src = u + 1 < S ? src + RS : src;  // the first backward stage is record S - 1 again
+      } else {
+        const bool tail = u > S;  // slab s = 2S - 1 - u < S - 1: O factors of record s + 1
+        mbar_expect(bars + b, (unsigned)((tail ? RS : LP) * sizeof(T)));
+        bulk_g2s(dst, src, (unsigned)(LP * sizeof(T)), bars + b);
+        if (tail) bulk_g2s(dst + LP, src + RS + LP, (unsigned)((RS - LP) * sizeof(T)), bars + b);
+        src -= RS;
       }
     }
-    pend |= 1u << b;
   };
-  auto wait = [&](int u) {
-    const int b = u & 1;
-    const bool ok = mbar_wait(bar + b, (ph >> b) & 1u);
-    ph ^= 1u << b;
-    pend &= ~(1u << b);
+  // the slot agrees on the outcome (a barrier of the slot): a stage counts
+  // as landed only if every thread saw it land.  wb / wpar: ring buffer and
+  // phase parity of the stage waited for next (stage u: u % P, (u / P) & 1)
+  int wb = 0;
+  unsigned wpar = 0u;
+  auto wait = [&]() {
+    const bool ok = !any(!mbar_wait(bars + wb, wpar, lim));
+    if (G == 1) __syncwarp();  // memory order across the warp, as the named barrier gives
     return ok;
   };
-  if (tid == 0) {
-    mbar_init(bar);
-    mbar_init(bar + 1);
+  auto wait_done = [&]() {  // advance to the next stage
+    if (++wb == P) {
+      wb = 0;
+      wpar ^= 1u;
+    }
+  };
+  if (lt == 0) {
+    for (int b = 0; b < P; ++b) mbar_init(bars + b);
     mbar_init_fence();
   }
-  vw[tid] = T(0);
-  __syncthreads();
+  sync();
+  for (int u = 0; u + 1 < P; ++u) issue_next();
   T rz = T(0), rr = T(0);
   bool bad = false;
+  int at = 0;  // the stage being waited for
   const int pl = zcol(MG, t) - t;
-  auto lower = [&](const T *Ls, const T *v) {  // (Linv v)_t
-    return bcast_dot<MG, T>(v, [&](int cc) { return cc <= t ? Ls[zcol(MG, cc) + t - cc] : T(0); });
+  // the products line block by line block, the block index a compile-time
+  // constant so that every packed offset folds: (Linv v)_t takes the blocks
+  // before this thread's line in full and its own block up to the diagonal
+  // (blocks after it are zero); (Linv^T v)_t its own block from the diagonal
+  // and the blocks after it in full
+  const int tl = act ? lane : 0;  // row within the line
+  auto lblock = [&](const T *Ls, const T *v, auto LJ, bool diag) {
+    constexpr int c0 = decltype(LJ)::value * M;
+    return bcast_dot<M, T>(v + 32 * decltype(LJ)::value, [&](int cc) {
+      return (!diag || cc <= tl) ? Ls[zcol(MG, c0 + cc) + t - c0 - cc] : T(0);
+    });
   };
-  auto upper = [&](const T *Ls, const T *v) {  // (Linv^T v)_t
-    return bcast_dot<MG, T>(v, [&](int cc) { return cc >= t ? Ls[pl + cc] : T(0); });
+  auto ublock = [&](const T *Ls, const T *v, auto LJ, bool diag) {
+    constexpr int c0 = decltype(LJ)::value * M;
+    return bcast_dot<M, T>(v + 32 * decltype(LJ)::value, [&](int cc) {
+      return (!diag || cc >= tl) ? Ls[pl + c0 + cc] : T(0);
+    });
   };
-  // sum over this thread's line of red[j][.]
-  auto line_sum = [&](int j) {
-    T s0 = T(0), s1 = T(0);
-#pragma unroll
-    for (int i = 0; i + 1 < M; i += 2) {
-      s0 += red[j * NT + lb + i];
-      s1 += red[j * NT + lb + i + 1];
+  using L0 = std::integral_constant<int, 0>;
+  using L1 = std::integral_constant<int, (G > 1 ? 1 : 0)>;
+  using L2 = std::integral_constant<int, (G > 2 ? 2 : 0)>;
+  using L3 = std::integral_constant<int, (G > 3 ? 3 : 0)>;
+  auto lower = [&](const T *Ls, const T *v) {
+    T acc = T(0);
+    if (li == 0) acc = lblock(Ls, v, L0{}, true);
+    if (G > 1 && li == 1) acc = lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, true);
+    if (G > 2 && li == 2) acc = (lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, false)) + lblock(Ls, v, L2{}, true);
+    if (G > 3 && li == 3)
+      acc = (lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, false)) +
+            (lblock(Ls, v, L2{}, false) + lblock(Ls, v, L3{}, true));
+    return acc;
+  };
+  auto upper = [&](const T *Ls, const T *v) {
+    T acc = T(0);
+    if (li == 0) {
+      acc = ublock(Ls, v, L0{}, true);
+      if (G > 1) acc += ublock(Ls, v, L1{}, false);
+      if (G > 2) acc += ublock(Ls, v, L2{}, false);
+      if (G > 3) acc += ublock(Ls, v, L3{}, false);
     }
-    if (M & 1) s0 += red[j * NT + lb + M - 1];
-    return s0 + s1;
+    if (G > 1 && li == 1) {
+      acc = ublock(Ls, v, L1{}, true);
+      if (G > 2) acc += ublock(Ls, v, L2{}, false);
+      if (G > 3) acc += ublock(Ls, v, L3{}, false);
+    }
+    if (G > 2 && li == 2) {
+      acc = ublock(Ls, v, L2{}, true);
+      if (G > 3) acc += ublock(Ls, v, L3{}, false);
+    }
+    if (G > 3 && li == 3) acc = ublock(Ls, v, L3{}, true);
+    return acc;
   };
-  issue(0);
   // forward sweep
   T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
   T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
-  T ylast = T(0);
-  for (int s = 0; s < S; ++s) {
-    if (s + 1 < total) issue(s + 1);
-    if (__syncthreads_or(!wait(s))) { bad = true; break; }
-    const T *Ls = buf0 + (s & 1) * RS, *XY = Ls + LP + 8 * t;
+  T w = T(0), ylast = T(0);
+  for (int s = 0; s < S; ++s, ++at) {
+    if (!wait()) { bad = true; break; }
+    const T *Ls = stage + (size_t)wb * RS, *XY = Ls + LP + 8 * t;
+    wait_done();
+    issue_next();  // every thread is past step s - 1: its buffer is free
+    const int par = s & 1;
     T rv = r0;
     if (UPD) {
       rv -= al * q0;
@@ -940,83 +1047,185 @@ zgroup_solve_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevMe
     }
     rr += rv * rv;
     T bv = rv;
-    if (s > 0) {  // bv -= (O_{s-1}^T w_{s-1})_t
-      const T wv = vw[tid];
-      red[0 * NT + tid] = act ? XY[4] * wv : T(0);
-      red[1 * NT + tid] = act ? XY[5] * wv : T(0);
-      red[2 * NT + tid] = act ? XY[6] * wv : T(0);
-      __syncthreads();
-      T o = XY[0] * vw[lb] + XY[1] * vw[lb + N] + XY[2] * vw[lb + 2 * N];
-      if (k == N - 1) o += line_sum(a);
+    if (s > 0) {  // bv -= (O_{s-1}^T w_{s-1})_t, line by line
+      const T x0 = XY[0], x1 = XY[1], x2 = XY[2];
+      const T s0 = warp_allsum(act ? XY[4] * w : T(0));
+      const T s1 = warp_allsum(act ? XY[5] * w : T(0));
+      const T s2 = warp_allsum(act ? XY[6] * w : T(0));
+      T o = x0 * __shfl_sync(0xffffffffu, w, 0) + x1 * __shfl_sync(0xffffffffu, w, N) +
+            x2 * __shfl_sync(0xffffffffu, w, 2 * N);
+      if (k == N - 1) o += a == 0 ? s0 : (a == 1 ? s1 : s2);
       bv -= o;
     }
-    vb[tid] = act ? bv : T(0);
-    __syncthreads();
-    T y = lower(Ls, vb);
+    if (act) vb(par)[lt] = bv;
+    sync();
+    T y = lower(Ls, vb(par));
     if (!act) y = T(0);
     rz += y * y;
-    if (act) z[gidx(s)] = y;
-    vy[tid] = y;
+    if (act) {
+      z[gidx(s)] = y;
+      vy(par)[lt] = y;
+    }
     ylast = y;
-    __syncthreads();
-    const T w = upper(Ls, vy);
-    vw[tid] = act ? w : T(0);
-    __syncthreads();  // vw complete; stage s is free
+    sync();
+    w = upper(Ls, vy(par));
+    if (!act) w = T(0);
   }
   // backward sweep
   if (!bad) {
     T y0 = ylast;
     T y1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
     T y2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
-    for (int s = S - 1; s >= 0; --s) {
-      const int u = 2 * S - 1 - s;
-      if (u + 1 < total) issue(u + 1);
-      if (__syncthreads_or(!wait(u))) { bad = true; break; }
-      const T *Ls = buf0 + (u & 1) * RS, *XY = Ls + LP + 8 * t;
+    T x = T(0);
+    for (int s = S - 1; s >= 0; --s, ++at) {
+      if (!wait()) { bad = true; break; }
+      const T *Ls = stage + (size_t)wb * RS, *XY = Ls + LP + 8 * t;
+      wait_done();
+      issue_next();
+      const int par = s & 1;
       T yv = y0;
       y0 = y1;
       y1 = y2;
       if (act && s >= 3) y2 = z[gidx(s - 3)];
       if (s + 1 < S) {  // yv -= (Linv_s O_s x_{s+1})_t
-        const T xv = vw[tid];
-        red[0 * NT + tid] = act ? XY[0] * xv : T(0);
-        red[1 * NT + tid] = act ? XY[1] * xv : T(0);
-        red[2 * NT + tid] = act ? XY[2] * xv : T(0);
-        __syncthreads();
-        T v = XY[4] * vw[lb + N - 1] + XY[5] * vw[lb + 2 * N - 1] + XY[6] * vw[lb + 3 * N - 1];
-        if (k == 0) v += line_sum(a);
-        vb[tid] = act ? v : T(0);
-        __syncthreads();
-        yv -= lower(Ls, vb);
+        const T s0 = warp_allsum(act ? XY[0] * x : T(0));
+        const T s1 = warp_allsum(act ? XY[1] * x : T(0));
+        const T s2 = warp_allsum(act ? XY[2] * x : T(0));
+        T v = XY[4] * __shfl_sync(0xffffffffu, x, N - 1) + XY[5] * __shfl_sync(0xffffffffu, x, 2 * N - 1) +
+              XY[6] * __shfl_sync(0xffffffffu, x, 3 * N - 1);
+        if (k == 0) v += a == 0 ? s0 : (a == 1 ? s1 : s2);
+        if (act) vb(par)[lt] = v;
+        sync();
+        yv -= lower(Ls, vb(par));
       }
-      vy[tid] = act ? yv : T(0);
-      __syncthreads();
-      T x = upper(Ls, vy);
+      if (act) vy(par)[lt] = yv;
+      sync();
+      x = upper(Ls, vy(par));
       if (!act) x = T(0);
       if (act) z[gidx(s)] = x;
-      vw[tid] = x;
-      __syncthreads();
     }
   }
-  if (bad) {  // a copy never landed: bounded waits for what is in flight, then report
-    if (pend & 1u) mbar_wait(bar, ph & 1u);
-    if (pend & 2u) mbar_wait(bar + 1, (ph >> 1) & 1u);
-    if (tid == 0 && err) atomicExch(err, 1);
+  if (bad) {  // a copy never landed: bounded waits for every copy in flight, then report
+    for (int u = at; u < issued; ++u) {
+      mbar_wait(bars + wb, wpar, kDrainNs);
+      wait_done();
+    }
+    if (lt == 0 && err) atomicExch(&err->flag, 1);
   }
-  __shared__ double rsum[2][4];
+  // the group's partial sums, in a fixed order
   double vrz = (double)rz, vrr = (double)rr;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     vrz += __shfl_xor_sync(0xffffffffu, vrz, o);
     vrr += __shfl_xor_sync(0xffffffffu, vrr, o);
   }
-  if ((tid & 31) == 0) { rsum[0][tid >> 5] = vrz; rsum[1][tid >> 5] = vrr; }
-  __syncthreads();
-  if (tid == 0) {
+  if (lane == 0) {
+    psum[(w0 + li) * 2] = vrz;
+    psum[(w0 + li) * 2 + 1] = vrr;
+  }
+  sync();
+  if (lt == 0) {
     double srz = 0.0, srr = 0.0;
-    for (int w = 0; w < NT / 32; ++w) { srz += rsum[0][w]; srr += rsum[1][w]; }
+    for (int ww = 0; ww < G; ++ww) {
+      srz += psum[(w0 + ww) * 2];
+      srr += psum[(w0 + ww) * 2 + 1];
+    }
     if (part_rz) part_rz[grp] = srz;
     if (part_rr) part_rr[grp] = srr;
+    for (int b = 0; b < P; ++b) mbar_inval(bars + b);  // every phase issued has completed
+  }
+}
+
+// packs [pk0, pk0 + npk) of one degree; CTAs take packs from queue[0]
+// (largest first); the last CTA to finish resets queue[0..1] for the next
+// launch.  One mesh (ginst == nullptr) or a batch (per group: its mirror's
+// mesh and first unknown).
+template <int N, typename T, bool UPD>
+__global__ void __launch_bounds__(kZgThreads)
+zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevMesh *__restrict__ meshes,
+                     const long long *__restrict__ dof_off, const int4 *__restrict__ glines,
+                     const long long *__restrict__ gfac, const int4 *__restrict__ packs, int pk0, int npk,
+                     int *__restrict__ queue, const T *__restrict__ fac, T *__restrict__ r,
+                     const T *__restrict__ q, T *__restrict__ z, const double *__restrict__ alpha,
+                     double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
+                     TnWait *__restrict__ err) {
+  if (done && *done) return;
+  constexpr int SW = zg_stage_per_warp<N, T>();
+  extern __shared__ __align__(16) unsigned char zsm[];
+  T *const stage0 = reinterpret_cast<T *>(zsm);
+  T *const vecs = stage0 + 4 * SW;
+  unsigned long long *const bars = reinterpret_cast<unsigned long long *>(vecs + 4 * kZgThreads);
+  __shared__ int s_pk;
+  __shared__ double psum[8];
+  const int warp = threadIdx.x >> 5;
+  const unsigned long long lim = wait_limit(err);
+  const T al = UPD ? (T)*alpha : T(0);
+  for (;;) {
+    if (threadIdx.x == 0) s_pk = atomicAdd(queue, 1);
+    __syncthreads();
+    const int pk = s_pk;
+    __syncthreads();
+    if (pk >= npk) break;
+    const int4 P4 = packs[pk0 + pk];
+    const int ent[4] = {P4.x, P4.y, P4.z, P4.w};
+    int w0 = 0, grp = -1, G = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int g = ent[i];
+      if (g < 0 || grp >= 0) continue;
+      const int4 L = glines[g];
+      const int gs = 1 + (L.y >= 0) + (L.z >= 0) + (L.w >= 0);
+      if (warp >= w0 && warp < w0 + gs) {
+        grp = g;
+        G = gs;
+      } else {
+        w0 += gs;
+      }
+    }
+    if (grp >= 0) {
+      int mncol = m1.ncol, mslab = m1.nslab;
+      T *rg = r, *zg = z;
+      const T *qg = q;
+      if (ginst) {
+        const int in = ginst[grp];
+        mncol = meshes[in].ncol;
+        mslab = meshes[in].nslab;
+        const long long o = dof_off[in];
+        rg += o;
+        zg += o;
+        if (UPD) qg += o;
+      }
+      T *stg = stage0 + (size_t)w0 * SW;
+      unsigned long long *sb = bars + kZgMaxStages * w0;
+      const int cap = G * SW;
+      switch (G) {
+        case 1:
+          zg_slot<N, 1, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+                                lim, err, part_rz, part_rr);
+          break;
+        case 2:
+          zg_slot<N, 2, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+                                lim, err, part_rz, part_rr);
+          break;
+        case 3:
+          zg_slot<N, 3, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+                                lim, err, part_rz, part_rr);
+          break;
+        default:
+          zg_slot<N, 4, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+                                lim, err, part_rz, part_rr);
+          break;
+      }
+    }
+    __syncthreads();  // every slot of the pack is done with shared memory
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+      __threadfence();
+    }
   }
 }
 
@@ -1039,7 +1248,7 @@ cudaError_t zline_smem_optin(K kernel, size_t bytes) {
 
 template <int N, typename T, bool UPD>
 cudaError_t solve_nt(const DevMesh &m, const void *fac, void *r, const void *q, void *z, const double *alpha,
-                     double *part_rz, double *part_rr, const int *done, int *zerr, cudaStream_t st) {
+                     double *part_rz, double *part_rr, const int *done, TnWait *zerr, cudaStream_t st) {
   const int blocks = (m.ncol * N * N + 3) / 4;
   constexpr size_t sm = zline_smem<N, T>();
   cudaError_t err = zline_smem_optin(zline_solve_kernel<N, T, T, UPD>, sm);
@@ -1051,7 +1260,7 @@ cudaError_t solve_nt(const DevMesh &m, const void *fac, void *r, const void *q, 
 
 template <int N>
 cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
-                    const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                    const double *alpha, double *part_rz, double *part_rr, const int *done, TnWait *zerr,
                     cudaStream_t st) {
   if (prec == TN_F64)
     return q ? solve_nt<N, double, true>(m, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st)
@@ -1063,7 +1272,7 @@ cudaError_t solve_n(const DevMesh &m, int prec, const void *fac, void *r, const 
 template <int N, typename T, bool UPD>
 cudaError_t solve_batch_nt(const DevMesh *meshes, const int2 *work, int nwork, const long long *fac_off,
                            const long long *dof_off, const void *fac, void *r, const void *q, void *z,
-                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, TnWait *zerr,
                            cudaStream_t st) {
   constexpr size_t sm = zline_smem<N, T>();
   cudaError_t err = zline_smem_optin(zline_solve_batch_kernel<N, T, T, UPD>, sm);
@@ -1077,7 +1286,7 @@ cudaError_t solve_batch_nt(const DevMesh *meshes, const int2 *work, int nwork, c
 template <int N>
 cudaError_t solve_batch_n(int prec, const DevMesh *meshes, const int2 *work, int nwork, const long long *fac_off,
                           const long long *dof_off, const void *fac, void *r, const void *q, void *z,
-                          const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                          const double *alpha, double *part_rz, double *part_rr, const int *done, TnWait *zerr,
                           cudaStream_t st) {
   if (prec == TN_F64)
     return q ? solve_batch_nt<N, double, true>(meshes, work, nwork, fac_off, dof_off, fac, r, q, z, alpha,
@@ -1109,41 +1318,43 @@ cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, int inst, cons
   return err;
 }
 
-template <int N, int G, typename T, bool UPD>
-cudaError_t zgroup_launch(const DevMesh &m, const ZGroupDev &gd, int cls, const void *fac, void *r, const void *q,
-                          void *z, const double *alpha, double *prz, double *prr, const int *done, int *zerr,
-                          cudaStream_t st) {
-  constexpr size_t sm = zg_smem<N, G, T>();
-  cudaError_t err = zline_smem_optin(zgroup_solve_kernel<N, G, T, UPD>, sm);
+template <int N, typename T, bool UPD>
+cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const void *fac, void *r, const void *q,
+                            void *z, const double *alpha, double *prz, double *prr, const int *done, TnWait *zerr,
+                            cudaStream_t st) {
+  constexpr size_t sm = zg_smem<N, T>();
+  auto kern = zgroup_packed_kernel<N, T, UPD>;
+  cudaError_t err = zline_smem_optin(kern, sm);
   if (err != cudaSuccess) return err;
-  zgroup_solve_kernel<N, G, T, UPD><<<gd.cls_n[cls], zg_threads<N, G>(), sm, st>>>(
-      m, gd.inst, gd.meshes, gd.dof_off, gd.lines, gd.fac_off, gd.cls_start[cls], (const T *)fac, (T *)r,
-      (const T *)q, (T *)z, alpha, prz, prr, done, zerr);
+  // persistent: as many CTAs as fit at once, never more than packs
+  static int per_sm[64] = {0};
+  int dev = 0;
+  err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!per_sm[dev]) {
+    int b = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kZgThreads, sm);
+    if (err != cudaSuccess) return err;
+    per_sm[dev] = b > 0 ? b : 1;
+  }
+  int grid = per_sm[dev] * tn_sm_count();
+  grid = grid < gd.pk_n[k] ? grid : gd.pk_n[k];
+  kern<<<grid, kZgThreads, sm, st>>>(m, gd.inst, gd.meshes, gd.dof_off, gd.lines, gd.fac_off, gd.packs,
+                                     gd.pk_start[k], gd.pk_n[k], gd.queue + 2 * k, (const T *)fac, (T *)r,
+                                     (const T *)q, (T *)z, alpha, prz, prr, done, zerr);
   return cudaGetLastError();
 }
 
-template <int N, int G>
-cudaError_t zgroup_launch_g(const DevMesh &m, const ZGroupDev &gd, int cls, int prec, const void *fac, void *r,
-                            const void *q, void *z, const double *alpha, double *prz, double *prr,
-                            const int *done, int *zerr, cudaStream_t st) {
-  if (prec == TN_F64)
-    return q ? zgroup_launch<N, G, double, true>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-             : zgroup_launch<N, G, double, false>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-  return q ? zgroup_launch<N, G, float, true>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-           : zgroup_launch<N, G, float, false>(m, gd, cls, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-}
-
 template <int N>
-cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int cls, int prec, const void *fac, void *r,
+cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int k, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *prz, double *prr,
-                            const int *done, int *zerr, cudaStream_t st) {
-  switch (gd.cls_G[cls]) {
-    case 1: return zgroup_launch_g<N, 1>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-    case 2: return zgroup_launch_g<N, 2>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-    case 3: return zgroup_launch_g<N, 3>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-    case 4: return zgroup_launch_g<N, 4>(m, gd, cls, prec, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-    default: return cudaErrorInvalidValue;
-  }
+                            const int *done, TnWait *zerr, cudaStream_t st) {
+  if (prec == TN_F64)
+    return q ? zgroup_launch_t<N, double, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+             : zgroup_launch_t<N, double, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+  return q ? zgroup_launch_t<N, float, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st)
+           : zgroup_launch_t<N, float, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st);
 }
 
 }  // namespace
@@ -1228,6 +1439,41 @@ bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *p, char *
       p->cls_n[p->ncls] = p->ngroups - start;
       ++p->ncls;
     }
+  // packs of groups filling the four warps of a CTA, per degree, largest
+  // first: 4, 3 + 1, 2 + 2, 2 + 1 + 1, 1 + 1 + 1 + 1 lines
+  for (int N = TN_MIN_N; N <= TN_MAX_N; ++N) {
+    std::vector<int> by[5];
+    for (int k = 0; k < p->ncls; ++k)
+      if (p->cls_N[k] == N)
+        for (int i = 0; i < p->cls_n[k]; ++i) by[p->cls_G[k]].push_back(p->cls_start[k] + i);
+    if (by[1].empty() && by[2].empty() && by[3].empty() && by[4].empty()) continue;
+    const int start = (int)p->packs.size();
+    size_t i1 = 0;
+    auto one = [&]() { return i1 < by[1].size() ? by[1][i1++] : -1; };
+    for (int g4 : by[4]) p->packs.push_back(make_int4(g4, -1, -1, -1));
+    for (int g3 : by[3]) p->packs.push_back(make_int4(g3, one(), -1, -1));
+    for (size_t i = 0; i < by[2].size(); i += 2) {
+      if (i + 1 < by[2].size()) {
+        p->packs.push_back(make_int4(by[2][i], by[2][i + 1], -1, -1));
+      } else {
+        const int a = one();
+        const int b = a >= 0 ? one() : -1;
+        p->packs.push_back(make_int4(by[2][i], a, b, -1));
+      }
+    }
+    while (i1 < by[1].size()) {
+      const int a = one(), b = one(), c = one(), d = one();
+      p->packs.push_back(make_int4(a, b, c, d));
+    }
+    if (p->npk >= kZgMaxPk) {
+      std::snprintf(msg, msglen, "too many degrees for the grouped-line solve");
+      return false;
+    }
+    p->pk_N[p->npk] = N;
+    p->pk_start[p->npk] = start;
+    p->pk_n[p->npk] = (int)p->packs.size() - start;
+    ++p->npk;
+  }
   return true;
 }
 
@@ -1258,15 +1504,17 @@ cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, con
   }
 }
 
-// the classes run concurrently: the first on st, the others round-robin on
-// side streams forked from and joined back into st (also inside a capture)
+// one launch per degree present (one for a single mesh): the first on st,
+// the others on side streams forked from and joined back into st (also
+// inside a capture)
 cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                            const int *done, int *zerr, cudaStream_t st) {
+                            const int *done, TnWait *zerr, cudaStream_t st) {
   const DevMesh one = m ? *m : DevMesh{};
-  cudaError_t err = cudaEventRecord(gd.fork, st);
+  cudaError_t err = cudaSuccess;
+  if (gd.npk > 1) err = cudaEventRecord(gd.fork, st);
   bool used[kZgSide] = {false};
-  for (int k = 0; k < gd.ncls && err == cudaSuccess; ++k) {
+  for (int k = 0; k < gd.npk && err == cudaSuccess; ++k) {
     cudaStream_t sk = st;
     if (k > 0) {
       const int sd = (k - 1) % kZgSide;
@@ -1277,7 +1525,7 @@ cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, con
         if (err != cudaSuccess) break;
       }
     }
-    switch (gd.cls_N[k]) {
+    switch (gd.pk_N[k]) {
 #define TN_CASE(NN)                                                                                        \
       case NN:                                                                                            \
         err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, sk); \
@@ -1323,7 +1571,7 @@ cudaError_t tn_zline_setup(const DevMesh &m, double *blk, float *fac, double *fa
 }
 
 cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
-                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, TnWait *zerr,
                            cudaStream_t st) {
   switch (m.N) {
 #define TN_CASE(NN) \
@@ -1337,7 +1585,7 @@ cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, void *r,
 cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const int2 *work, int nwork,
                                  const long long *fac_off, const long long *dof_off, const void *fac, void *r,
                                  const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                                 const int *done, int *zerr, cudaStream_t st) {
+                                 const int *done, TnWait *zerr, cudaStream_t st) {
   if (nwork <= 0) return cudaSuccess;
   switch (N) {
 #define TN_CASE(NN)                                                                                   \

@@ -27,7 +27,8 @@
 
 namespace {
 
-constexpr int kRedBlocks = 8 * 152;  // fixed partition of the vector reductions
+// fixed partition of the vector reductions: 8 blocks per SM of the device
+int red_blocks() { return 8 * tn_sm_count(); }
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -384,6 +385,7 @@ __global__ void k_init_scalars_split(tn_pcg_scalars *s, const double *rzp, int n
 namespace tn {
 
 thread_local long long g_launches = 0;
+thread_local bool g_timed_out = false;
 
 #define TN_CU(call)                                   \
   do {                                                \
@@ -393,8 +395,8 @@ thread_local long long g_launches = 0;
 
 cudaError_t pcg_setup_dinv(size_t n, const double *diag, void *dinv, int prec, cudaStream_t st) {
   g_launches += 1;
-  if (prec == TN_F64) k_invert<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (double *)dinv);
-  else k_invert<float><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (float *)dinv);
+  if (prec == TN_F64) k_invert<double><<<red_blocks(), kRedThreads, 0, st>>>(n, diag, (double *)dinv);
+  else k_invert<float><<<red_blocks(), kRedThreads, 0, st>>>(n, diag, (float *)dinv);
   return cudaGetLastError();
 }
 
@@ -405,12 +407,12 @@ static cudaError_t pcg_iteration(const OpSys &sys, int prec, size_t n, PcgVector
   TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
   k_alpha<<<1, 1024, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
-  k_update<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (T *)v.z, (const T *)v.p,
+  k_update<T><<<red_blocks(), kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.r, (T *)v.z, (const T *)v.p,
                                                   (const T *)v.q, (const T *)v.dinv, part_red);
   TN_CU(cudaGetLastError());
-  k_beta<<<1, 1024, 0, st>>>(s, part_red, kRedBlocks);
+  k_beta<<<1, 1024, 0, st>>>(s, part_red, red_blocks());
   TN_CU(cudaGetLastError());
-  k_pupdate<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
+  k_pupdate<T><<<red_blocks(), kRedThreads, 0, st>>>(s, n, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
 }
 
@@ -424,7 +426,7 @@ static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, Pcg
   TN_CU(sys.zsolve(prec, v.zfac, v.r, v.q, v.z, &s->alpha, v.part_rz, &s->done, st));
   k_beta_split<<<1, 1024, 0, st>>>(s, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts, sys.n_rz_parts);
   TN_CU(cudaGetLastError());
-  k_pupdate_x<T><<<kRedBlocks, kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.p, (const T *)v.z);
+  k_pupdate_x<T><<<red_blocks(), kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.p, (const T *)v.z);
   return cudaGetLastError();
 }
 
@@ -438,7 +440,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   const bool zl = v.zfac != nullptr;
   g_launches += zl ? 5 : 3;
   if (x0_zero) {
-    k_fill<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.x, T(0));
+    k_fill<T><<<red_blocks(), kRedThreads, 0, st>>>(n, (T *)v.x, T(0));
     TN_CU(cudaGetLastError());
   } else {
     TN_CU(sys.apply(prec, v.x, v.q, nullptr, st));
@@ -446,18 +448,18 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   }
   const T *Ax = x0_zero ? nullptr : (const T *)v.q;
   if (zl) {
-    k_init_r<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, part_red);
+    k_init_r<T><<<red_blocks(), kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, part_red);
     TN_CU(cudaGetLastError());
     TN_CU(sys.zsolve(prec, v.zfac, v.r, nullptr, v.z, nullptr, v.part_rz, nullptr, st));
-    k_copy<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (T *)v.p, (const T *)v.z);
+    k_copy<T><<<red_blocks(), kRedThreads, 0, st>>>(n, (T *)v.p, (const T *)v.z);
     TN_CU(cudaGetLastError());
     k_init_scalars_split<<<1, 256, 0, st>>>(s_dev, v.part_rz, sys.n_rz_parts, v.part_rz + sys.n_rz_parts,
                                             sys.n_rz_parts, rtol * rtol, max_iters);
   } else {
-    k_init<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, (T *)v.z, (T *)v.p,
+    k_init<T><<<red_blocks(), kRedThreads, 0, st>>>(n, (const T *)v.b, Ax, (T *)v.r, (T *)v.z, (T *)v.p,
                                                   (const T *)v.dinv, part_red);
     TN_CU(cudaGetLastError());
-    k_init_scalars<<<1, 256, 0, st>>>(s_dev, part_red, kRedBlocks, rtol * rtol, max_iters);
+    k_init_scalars<<<1, 256, 0, st>>>(s_dev, part_red, red_blocks(), rtol * rtol, max_iters);
   }
   TN_CU(cudaGetLastError());
   TN_CU(cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st));
@@ -517,8 +519,15 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
     if (err != cudaSuccess) break;
     err = cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st);
     if (err != cudaSuccess) break;
+    int waitflag = 0;
+    if (sys.zerr) err = cudaMemcpyAsync(&waitflag, &sys.zerr->flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) break;
     err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) break;
+    if (waitflag) {  // a line solve gave up on its staged factors: the run is void
+      g_timed_out = true;
+      break;
+    }
     if (s_host->done) break;
     if (hook.fn && hook.fn(hook.user)) break;
     // stagnation: the recursive residual has not halved for 40 chunks
@@ -548,9 +557,9 @@ cudaError_t residual_f64(const OpSys &sys, size_t n, const double *b, const doub
                          double *part_red, double *sum_dev, double *rr_host, cudaStream_t st) {
   g_launches += 3;
   TN_CU(sys.apply(TN_F64, x, Ax, nullptr, st));
-  k_residual<<<kRedBlocks, kRedThreads, 0, st>>>(n, b, Ax, r, part_red);
+  k_residual<<<red_blocks(), kRedThreads, 0, st>>>(n, b, Ax, r, part_red);
   TN_CU(cudaGetLastError());
-  k_finish_sum<<<1, 256, 0, st>>>(part_red, kRedBlocks, sum_dev);
+  k_finish_sum<<<1, 256, 0, st>>>(part_red, red_blocks(), sum_dev);
   TN_CU(cudaGetLastError());
   double tmp[2];
   TN_CU(cudaMemcpyAsync(tmp, sum_dev, sizeof(tmp), cudaMemcpyDeviceToHost, st));
@@ -562,9 +571,9 @@ cudaError_t residual_f64(const OpSys &sys, size_t n, const double *b, const doub
 cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_dev, double *out_host,
                       cudaStream_t st) {
   g_launches += 2;
-  k_sumsq<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, v, part_red);
+  k_sumsq<double><<<red_blocks(), kRedThreads, 0, st>>>(n, v, part_red);
   TN_CU(cudaGetLastError());
-  k_finish_sum<<<1, 256, 0, st>>>(part_red, kRedBlocks, sum_dev);
+  k_finish_sum<<<1, 256, 0, st>>>(part_red, red_blocks(), sum_dev);
   TN_CU(cudaGetLastError());
   double tmp[2];
   TN_CU(cudaMemcpyAsync(tmp, sum_dev, sizeof(tmp), cudaMemcpyDeviceToHost, st));
@@ -575,23 +584,23 @@ cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_d
 
 cudaError_t cast_scaled(size_t n, const double *r64, double scale, float *r32, float *d32, cudaStream_t st) {
   g_launches += 1;
-  k_cast_scaled<<<kRedBlocks, kRedThreads, 0, st>>>(n, r64, scale, r32, d32);
+  k_cast_scaled<<<red_blocks(), kRedThreads, 0, st>>>(n, r64, scale, r32, d32);
   return cudaGetLastError();
 }
 
 cudaError_t refine_update(size_t n, double *x, const float *d, double scale, cudaStream_t st) {
   g_launches += 1;
-  k_refine<<<kRedBlocks, kRedThreads, 0, st>>>(n, x, d, scale);
+  k_refine<<<red_blocks(), kRedThreads, 0, st>>>(n, x, d, scale);
   return cudaGetLastError();
 }
 
 cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st) {
   g_launches += 1;
-  k_fill<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, v, val);
+  k_fill<double><<<red_blocks(), kRedThreads, 0, st>>>(n, v, val);
   return cudaGetLastError();
 }
 
-int reduction_blocks() { return kRedBlocks; }
+int reduction_blocks() { return red_blocks(); }
 
 }  // namespace tn
 
@@ -625,13 +634,13 @@ namespace tn {
 cudaError_t multidot(size_t n, const double *a, const double *const *B_dev, int nb, double *part, double *host_tmp,
                      double *out, cudaStream_t st) {
   g_launches += 1;
-  k_multidot<<<kRedBlocks, kRedThreads, 0, st>>>(n, a, B_dev, nb, part);
+  k_multidot<<<red_blocks(), kRedThreads, 0, st>>>(n, a, B_dev, nb, part);
   TN_CU(cudaGetLastError());
-  TN_CU(cudaMemcpyAsync(host_tmp, part, sizeof(double) * nb * kRedBlocks, cudaMemcpyDeviceToHost, st));
+  TN_CU(cudaMemcpyAsync(host_tmp, part, sizeof(double) * nb * red_blocks(), cudaMemcpyDeviceToHost, st));
   TN_CU(cudaStreamSynchronize(st));
   for (int j = 0; j < nb; ++j) {
     double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += host_tmp[(size_t)j * kRedBlocks + b];
+    for (int b = 0; b < red_blocks(); ++b) s += host_tmp[(size_t)j * red_blocks() + b];
     out[j] = s;
   }
   return cudaSuccess;
@@ -640,28 +649,28 @@ cudaError_t multidot(size_t n, const double *a, const double *const *B_dev, int 
 cudaError_t fcg_orth(size_t n, const double *z, const double *q, const double *const *P, const double *const *AP,
                      const double *beta, int nb, double *p, double *Ap, cudaStream_t st) {
   g_launches += 1;
-  k_fcg_orth<<<kRedBlocks, kRedThreads, 0, st>>>(n, z, q, P, AP, beta, nb, p, Ap);
+  k_fcg_orth<<<red_blocks(), kRedThreads, 0, st>>>(n, z, q, P, AP, beta, nb, p, Ap);
   return cudaGetLastError();
 }
 
 cudaError_t fcg_step(size_t n, double alpha, const double *p, const double *Ap, double *x, double *r,
                      cudaStream_t st) {
   g_launches += 1;
-  k_fcg_step<<<kRedBlocks, kRedThreads, 0, st>>>(n, alpha, p, Ap, x, r);
+  k_fcg_step<<<red_blocks(), kRedThreads, 0, st>>>(n, alpha, p, Ap, x, r);
   return cudaGetLastError();
 }
 
 cudaError_t upcast(size_t n, const float *d, double scale, double *z, cudaStream_t st) {
   g_launches += 1;
-  k_upcast<<<kRedBlocks, kRedThreads, 0, st>>>(n, d, scale, z);
+  k_upcast<<<red_blocks(), kRedThreads, 0, st>>>(n, d, scale, z);
   return cudaGetLastError();
 }
 
 }  // namespace tn
 
 cudaError_t tn_jacobi_apply(size_t n, int prec, const double *diag, const void *r, void *z, cudaStream_t st) {
-  if (prec == TN_F64) k_jacobi<double><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (const double *)r, (double *)z);
-  else k_jacobi<float><<<kRedBlocks, kRedThreads, 0, st>>>(n, diag, (const float *)r, (float *)z);
+  if (prec == TN_F64) k_jacobi<double><<<red_blocks(), kRedThreads, 0, st>>>(n, diag, (const double *)r, (double *)z);
+  else k_jacobi<float><<<red_blocks(), kRedThreads, 0, st>>>(n, diag, (const float *)r, (float *)z);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,17 @@ struct DevMesh {
   const double *d_layer_c = nullptr;  // [n_layers][3]: d(c11, c12, c44)/dtheta
 };
 
+// bounded device waits (the staging waits of the line solves): the kernels
+// read limit_ns and give up a wait after that many nanoseconds of
+// %globaltimer, set flag = 1, wait (bounded again) for their copies still in
+// flight and return; the host reports TN_ETIMEOUT.  Lives in device memory.
+struct TnWait {
+  unsigned long long limit_ns;
+  int flag;
+  int pad;
+};
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // 1 s
+
 // forward-mode dual number (value, derivative along one direction)
 struct Dual {
   double v, d;
@@ -101,6 +112,9 @@ struct HostMesh {
 tn_status build_host_mesh(const tn_mesh_desc *d, HostMesh *out, char *msg, int msglen);
 void free_host_mesh(HostMesh *m);
 }  // namespace tn
+
+// streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount)
+int tn_sm_count();
 
 // kernels (kernels.cu) -- launchers return cudaError_t of the launch
 cudaError_t tn_upload_lgl(const LglTables *t);

@@ -18,7 +18,7 @@ cudaError_t tn_zline_setup(const DevMesh &m, double *blk, float *fac, double *fa
 // partial r.z, part_rr[b] = partial r.r (either may be nullptr).  *done != 0:
 // returns at once.  A staging wait that runs out sets *zerr = 1.
 cudaError_t tn_zline_solve(const DevMesh &m, int prec, const void *fac, void *r, const void *q, void *z,
-                           const double *alpha, double *part_rz, double *part_rr, const int *done, int *zerr,
+                           const double *alpha, double *part_rz, double *part_rr, const int *done, TnWait *zerr,
                            cudaStream_t st);
 cudaError_t tn_upload_lgl_precond(const LglTables *t);
 // batch: warp w of block b solves line work[4 b + w] = (instance, line); factors of
@@ -26,11 +26,12 @@ cudaError_t tn_upload_lgl_precond(const LglTables *t);
 cudaError_t tn_zline_solve_batch(int N, int prec, const DevMesh *meshes, const int2 *work, int nwork,
                                  const long long *fac_off, const long long *dof_off, const void *fac, void *r,
                                  const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                                 const int *done, int *zerr, cudaStream_t st);
+                                 const int *done, TnWait *zerr, cudaStream_t st);
 
 // ---- line groups: lines joined by matching nodes of lateral faces
 constexpr int kZgMaxCls = 28;  // classes: (group size 1..4) x (N = 3..9)
-constexpr int kZgSide = 6;     // side streams the classes run on
+constexpr int kZgMaxPk = 7;    // pack lists: one per degree (N = 3..9), one launch each
+constexpr int kZgSide = 6;     // side streams the launches of a batch run on
 // the groups of one mesh or of every mirror of a batch, ordered by class
 // (group size, largest first; then N; then mirror)
 struct ZGroupPlan {
@@ -42,6 +43,11 @@ struct ZGroupPlan {
   int ncls = 0;
   int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
   std::vector<int> inst_start, inst_n;  // [mirror * 5 + g]: first group and count of size g (set-up)
+  // packs: up to four groups filling the four warps of a CTA (-1: none),
+  // per degree, largest first
+  std::vector<int4> packs;
+  int npk = 0;
+  int pk_N[kZgMaxPk] = {0}, pk_start[kZgMaxPk] = {0}, pk_n[kZgMaxPk] = {0};
 };
 // device view of a plan and the streams the classes run on
 struct ZGroupDev {
@@ -52,6 +58,10 @@ struct ZGroupDev {
   const long long *dof_off = nullptr;  // batch: first unknown of every mirror (device)
   int ngroups = 0, ncls = 0;
   int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
+  const int4 *packs = nullptr;         // the plan's packs (device)
+  int *queue = nullptr;                // per degree: next pack, CTAs finished (device, zero between launches)
+  int npk = 0;
+  int pk_N[kZgMaxPk] = {0}, pk_start[kZgMaxPk] = {0}, pk_n[kZgMaxPk] = {0};
   cudaStream_t side[kZgSide] = {nullptr};
   cudaEvent_t fork = nullptr, join[kZgSide] = {nullptr};
 };
@@ -67,4 +77,4 @@ cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, con
 // partial sums: one per group
 cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                            const int *done, int *zerr, cudaStream_t st);
+                            const int *done, TnWait *zerr, cudaStream_t st);

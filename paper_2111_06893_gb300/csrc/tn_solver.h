@@ -32,7 +32,7 @@ struct OpSys {
   int gvar[8] = {0};      // the same per degree group of a batch
   int n_apply_parts = 0;  // partial sums written by one apply
   int n_rz_parts = 0;     // partial sums of r.z written by one z-line solve (r.r: as many, after them)
-  int *zerr = nullptr;    // set to 1 by a z-line solve whose staging wait ran out
+  TnWait *zerr = nullptr; // wait limit of the line solves; flag set by one whose staging wait ran out
   bool grouped = false;   // grouped lines (zg) instead of single lines
   ZGroupDev zg;
   cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const;
@@ -61,6 +61,8 @@ struct ChunkHook {
 namespace tn {
 // kernel launches issued on behalf of the current solve (host counter)
 extern thread_local long long g_launches;
+// set by a PCG run that stopped because a line solve's bounded wait ran out
+extern thread_local bool g_timed_out;
 cudaError_t pcg_setup_dinv(size_t n, const double *diag, void *dinv, int prec, cudaStream_t st);
 cudaError_t pcg_f64(const OpSys &sys, size_t n, PcgVectors &v, bool x0_zero, double rtol, int max_iters,
                     int chunk, tn_pcg_scalars *s_dev, tn_pcg_scalars *s_host, double *part_elem,

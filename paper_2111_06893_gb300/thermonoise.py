@@ -24,13 +24,14 @@ TN_PC_JACOBI, TN_PC_ZLINE, TN_PC_ZGROUP = 0, 1, 2
 PRECONDS = {"jacobi": TN_PC_JACOBI, "zline": TN_PC_ZLINE, "zgroup": TN_PC_ZGROUP}
 STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ECUDA", -4: "TN_ENOTCONV",
           -5: "TN_EBREAKDOWN", -6: "TN_ETIMEOUT", -7: "TN_ESTATE"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
 
 # every entry point declared in include/thermonoise.h
 SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof",
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
            "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes",
-           "tn_apply_tuning", "tn_set_apply_variant"]
+           "tn_apply_tuning", "tn_set_apply_variant", "tn_iso_moduli", "tn_fma_peak"]
 
 
 class MeshDesc(C.Structure):
@@ -52,7 +53,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
                 ("use_x0", C.c_int), ("check_every", C.c_int), ("inner_max", C.c_int),
-                ("fcg_window", C.c_int), ("energy_rtol", C.c_double)]
+                ("fcg_window", C.c_int), ("energy_rtol", C.c_double),
+                ("device_wait_limit_s", C.c_double)]
 
 
 class SolveReport(C.Structure):
@@ -97,6 +99,8 @@ def load():
         "tn_solve": (C.c_int, [vp, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
         "tn_layer_energies": (C.c_int, [vp, vp, dp]),
         "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
+        "tn_iso_moduli": (C.c_int, [C.c_double, C.c_double, dp, dp]),
+        "tn_fma_peak": (C.c_int, [C.c_int, C.c_int, dp]),
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
         "tn_precond_factor_bytes": (C.c_int, [vp, C.c_int, C.POINTER(C.c_longlong)]),
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
@@ -349,7 +353,7 @@ class Context:
 
     def solve(self, mode="f64", rtol=1e-12, inner_rtol=1e-3, max_iter=200000, max_outer=5000,
               x0=None, check_every=25, out=None, raise_on_error=True, precond=None,
-              energy_rtol=0.0, inner_max=None, fcg_window=16):
+              energy_rtol=0.0, inner_max=None, fcg_window=16, device_wait_limit_s=0.0):
         """precond None: grouped lines.  inner_max None: the library's
         default, 40 FP32 iterations per flexible-CG step with grouped lines
         and 300 otherwise (measured best on the single-coating, crystalline
@@ -362,6 +366,7 @@ class Context:
         o.max_iter, o.max_outer, o.check_every = max_iter, max_outer, check_every
         o.energy_rtol = energy_rtol
         o.inner_max, o.fcg_window = inner_max or 0, fcg_window
+        o.device_wait_limit_s = device_wait_limit_s
         u = out if out is not None else self._vec(self._torch.float64)
         o.use_x0 = 0
         if x0 is not None:
@@ -394,6 +399,13 @@ def noise_psd(U, phi, kB_T, f, F0):
     return out.value
 
 
+def fma_peak(device=0, precision="f32"):
+    """Measured FMA peak of the CUDA cores in flop/s (tn_fma_peak)."""
+    out = C.c_double()
+    _check(load().tn_fma_peak(int(device), TN_F32 if precision == "f32" else TN_F64, C.byref(out)))
+    return out.value
+
+
 def setup(desc, device=0, stream=None):
     """Context with mesh, materials and beam of a workload description."""
     ctx = Context(device, stream)
@@ -403,13 +415,17 @@ def setup(desc, device=0, stream=None):
     return ctx
 
 
-def iso_moduli(Y, nu):
-    """(c11, c12, c44) = (lambda + 2 mu, lambda, mu) from Young's modulus and
-    Poisson ratio (the footnote to Eq. (constrel_iso)); works on floats and on
-    torch tensors (differentiably)."""
-    mu = Y / (2.0 * (1.0 + nu))
-    lam = Y * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
-    return lam + 2.0 * mu, lam, mu
+def iso_moduli(Y, nu, derivatives=False):
+    """(c11, c12, c44) of an isotropic material from the library
+    (tn_iso_moduli); with derivatives=True also the 3 x 2 matrix
+    d(c11, c12, c44)/d(Y, nu)."""
+    c = (C.c_double * 3)()
+    dc = (C.c_double * 6)()
+    _check(load().tn_iso_moduli(float(Y), float(nu), c, dc))
+    cs = (c[0], c[1], c[2])
+    if not derivatives:
+        return cs
+    return cs, np.array(dc[:], dtype=np.float64).reshape(3, 2)
 
 
 def _energy_fn_class():

@@ -71,3 +71,22 @@ def test_apply_tuning_entry_points_reject_null_context(lib):
     var = (C.c_int * 7)()
     assert lib.tn_apply_tuning(None, var, None) != 0
     assert lib.tn_set_apply_variant(None, 6, 0) != 0
+
+
+def test_iso_moduli_host_entry_point(lib):
+    """tn_iso_moduli against the oracle's Lame conversion (written from the
+    other direction of the footnote to Eq. (constrel_iso)) and its
+    derivatives against complex steps of the oracle's formula."""
+    from oracle import materials
+    from paper_2111_06893_gb300 import thermonoise
+    for Y, nu in [(72e9, 0.17), (140e9, 0.23), (3.0, -0.4)]:
+        (c11, c12, c44), dc = thermonoise.iso_moduli(Y, nu, derivatives=True)
+        lam, mu = materials.lame_from_young(Y, nu)
+        assert np.allclose([c11, c12, c44], [lam + 2 * mu, lam, mu], rtol=1e-14, atol=0)
+        h = 1e-30
+        for j, (dY, dn) in enumerate([(1j * h, 0.0), (0.0, 1j * h)]):
+            l2, m2 = materials.lame_from_young(Y + dY, nu + dn)
+            ref = np.imag([l2 + 2 * m2, l2, m2]) / h
+            assert np.allclose(dc[:, j], ref, rtol=1e-13, atol=0), (j, dc[:, j], ref)
+    with pytest.raises(thermonoise.ThermonoiseError):
+        thermonoise.iso_moduli(72e9, 0.5)
