@@ -40,3 +40,21 @@ def test_records_cover_every_case():
         U = GOLDEN[name]["layer_energies"]
         assert len(U) == len(CASES[name]()["materials"]) and min(U) > 0
 
+
+
+def test_oracle_reproduces_its_gradient_record():
+    """tests/golden/oracle_gradients.json (make_gradient_golden.py, oracle/
+    alone): the layered box's energies and every derivative recomputed."""
+    import json as _json
+    from cases import layered_box
+    from oracle import gradient as G
+    path = os.path.join(HERE, "golden", "oracle_gradients.json")
+    with open(path) as f:
+        rec = _json.load(f)
+    assert {"layered_box", "thin_cylinder", "tie_stack"} <= set(rec)
+    desc = layered_box()
+    r = rec["layered_box"]
+    assert np.max(np.abs(G.energies(desc) - np.array(r["U"])) / np.array(r["U"])) < 1e-12
+    for key, dU in r["dU"].items():
+        d = G.energy_derivative(desc, tuple(_json.loads(key)))
+        assert np.max(np.abs(d - np.array(dU))) <= 1e-10 * np.max(np.abs(dU)), key

@@ -1,14 +1,47 @@
-"""Adjoint energy gradients on the GPU against the oracle's complex-step
-gradients (exact derivatives of the discrete energies) and against central
-finite differences of GPU solves."""
+"""Adjoint energy gradients on the GPU against the oracle's exact derivatives
+(complex step through the whole oracle with iteratively refined solves,
+tests/golden/oracle_gradients.json written by make_gradient_golden.py from
+oracle/ alone) and against finite differences of GPU solves.
+
+Tolerances are the measured error plus margin, each with its cause:
+  layered_box    well conditioned: GPU gradients agree with the oracle to
+                 ~2e-13; tested at 1e-11.
+  thin_cylinder  0.02 / 0.05-thick coatings, cond(A) ~ 1e8: GPU energies
+                 agree to ~2e-10 and gradients to ~6e-9 whatever the solver
+                 (PCG to the FP64 floor, column or grouped lines, Jacobi,
+                 mixed).  An FP64 perturbation of the oracle's own operator
+                 (each entry times 1 + 1e-15 N(0,1)) moves its energies by up
+                 to 1.7e-9 and its gradients by 0.5-3.7e-9: the gap is the
+                 rounding floor of the discrete problem in FP64, not the
+                 solver.  Energies tested at 1e-9, gradients at 1e-8.
+  tie_stack      four equal cubic layers of 2^-11 (exact ties of
+                 min(h_int, h_ext); both sides take the derivative for an
+                 increasing parameter there), FP64 residual floor ~3e-9:
+                 GPU energies agree to ~4e-9 and gradients to ~3e-5.  The
+                 same perturbation of the oracle's operator (1 + 2e-16 or
+                 1e-15 N(0,1) per entry) moves its energies by 5e-9 to 1e-7
+                 and its gradients in slab positions and c11 by 1.4e-5 to
+                 2.7e-4 (r0: 5e-9 to 3e-8): again the floor of the discrete
+                 problem in FP64.  Energies tested at 2e-8, gradients at 1e-4.
+"""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import gradient as G
+from cases import layered_box, thin_cylinder, tie_stack
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def golden():
+    with open(os.path.join(HERE, "golden", "oracle_gradients.json")) as f:
+        return json.load(f)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -19,74 +52,91 @@ def built():
     build.build()
 
 
-def layered_box():
-    return W.box([-1.0, 0.2, 1.0], [-0.5, 1.0], [0.0, -0.3, -0.8, -1.3], 3, None, slab_layer=[0, 1, 2],
-                 materials=[W.CRYSTAL_A, W.COATING_HIGH, W.FUSED_SILICA], penalty_C=3.0,
-                 bc_side="fixed", bc_bottom="fixed", r0=0.7)
-
-
-def thin_cylinder():
-    d = W.cylinder(10.0, 10.0, [0.02, 0.05], [W.CRYSTAL_B, W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 2,
-                   r0=1.3)
-    # geometric substrate slabs share one depth ratio, so the face sizes h
-    # of the two slabs meeting at the inner substrate boundary are equal and
-    # min(h, h_ext) has a kink there: the energies have only one-sided
-    # derivatives in slab_z[2] and slab_z[3].  Moving that boundary off the
-    # geometric sequence makes every slab derivative two-sided.
-    z = list(d["slab_z"])
-    z[3] = -0.9
-    d["slab_z"] = z
-    return d
-
-
-def iso_chain(m):
-    """d(c11, c12, c44)/d(Y, nu) for an isotropic material."""
-    Y, nu = m["Y"], m["nu"]
-    h = 1e-7
-    from paper_2111_06893_gb300.thermonoise import iso_moduli
-    base = np.array(iso_moduli(Y, nu))
-    dY = (np.array(iso_moduli(Y * (1 + h), nu)) - np.array(iso_moduli(Y * (1 - h), nu))) / (2 * h * Y)
-    dn = (np.array(iso_moduli(Y, nu + h)) - np.array(iso_moduli(Y, nu - h))) / (2 * h)
-    return base, dY, dn
-
-
-# tolerance: the layered box is well conditioned (both solves accurate to
-# ~1e-13); the thin-coating cylinder (C = 100, 0.02-thick layers) has
-# cond(A) ~ 1e8, so both the oracle's direct solve and the GPU solves carry
-# ~1e-8 relative error into u and lambda
-@pytest.mark.parametrize("make,tol", [(layered_box, 1e-8), (thin_cylinder, 1e-6)])
-def test_adjoint_gradient_matches_oracle_complex_step(make, tol):
+def gpu_gradient(ctx, desc, w, mode="f64"):
+    """dJ/dtheta for every parameter of the golden record, J = w . U."""
     from paper_2111_06893_gb300 import thermonoise
-    desc = make()
-    ctx = thermonoise.setup(desc)
-    # thin layers put the FP64 residual floor near 1e-11: stop on energies
-    u, rep = ctx.solve(mode="f64", rtol=1e-13, energy_rtol=1e-14, raise_on_error=False)
-    assert rep["rel_residual"] < 1e-10, rep
-    nl = len(desc["materials"])
-    rng = np.random.default_rng(4)
-    w = rng.uniform(0.5, 2.0, size=nl)
-    g = ctx.energy_grad(u, w, mode="f64", rtol=1e-13, raise_on_error=False)
-    assert g["report"]["rel_residual"] < 1e-10, g["report"]
+    g = ctx.energy_grad(ctx._u, w, mode=mode, rtol=1e-15, raise_on_error=False)
+    out = {}
     ns = len(desc["slab_z"]) - 1
-    # slab boundaries
     for s in range(1, ns + 1):
-        ref = float(np.dot(w, G.energy_derivative(desc, ("slab_z", s))))
-        scale = max(abs(ref), 1e-3 * max(abs(v) for v in g["slab_z"]))
-        assert abs(g["slab_z"][s] - ref) <= tol * scale, ("slab_z", s, g["slab_z"][s], ref)
-    ref = float(np.dot(w, G.energy_derivative(desc, ("r0",))))
-    assert abs(g["r0"] - ref) <= tol * abs(ref), ("r0", g["r0"], ref)
-    # moduli: cubic layers directly, isotropic through (Y, nu)
+        out[json.dumps(["slab_z", s])] = g["slab_z"][s]
+    out[json.dumps(["r0"])] = g["r0"]
     for L, m in enumerate(desc["materials"]):
         if m["kind"] == "cubic":
             for q, key in enumerate(["c11", "c12", "c44"]):
-                ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
-                assert abs(g["moduli"][L, q] - ref) <= tol * abs(ref), (L, key, g["moduli"][L, q], ref)
+                out[json.dumps(["material", L, key])] = g["moduli"][L, q]
         else:
-            _, dY, dn = iso_chain(m)
-            for key, dc in (("Y", dY), ("nu", dn)):
-                ref = float(np.dot(w, G.energy_derivative(desc, ("material", L, key))))
-                got = float(np.dot(g["moduli"][L], dc))
-                assert abs(got - ref) <= max(tol, 1e-6) * abs(ref), (L, key, got, ref)
+            _, dc = thermonoise.iso_moduli(m["Y"], m["nu"], derivatives=True)  # d(c11, c12, c44)/d(Y, nu)
+            out[json.dumps(["material", L, "Y"])] = float(np.dot(g["moduli"][L], dc[:, 0]))
+            out[json.dumps(["material", L, "nu"])] = float(np.dot(g["moduli"][L], dc[:, 1]))
+    return out, g["report"]
+
+
+CASES = {"layered_box": (layered_box, 1e-12, 1e-11),
+         "thin_cylinder": (thin_cylinder, 1e-9, 1e-8),
+         "tie_stack": (tie_stack, 2e-8, 1e-4)}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_energies_and_adjoint_gradients_match_refined_oracle(name):
+    from paper_2111_06893_gb300 import thermonoise
+    make, tol_U, tol_g = CASES[name]
+    desc = make()
+    rec = golden()[name]
+    ctx = thermonoise.setup(desc)
+    # FP64 PCG run to its rounding floor (stagnation of the true residual)
+    u, rep = ctx.solve(mode="f64", rtol=1e-15, raise_on_error=False)
+    assert rep["status"] in (0, thermonoise.STATUS_CODE["TN_ENOTCONV"]), rep
+    U = ctx.layer_energies(u)
+    Uo = np.array(rec["U"])
+    errU = np.max(np.abs(U - Uo) / Uo)
+    assert errU <= tol_U, (errU, U, Uo)
+    ctx._u = u
+    w = np.random.default_rng(4).uniform(0.5, 2.0, size=len(desc["materials"]))
+    got, grep = gpu_gradient(ctx, desc, w)
+    assert grep["status"] in (0, thermonoise.STATUS_CODE["TN_ENOTCONV"]), grep
+    errs = {}
+    for key, dU in rec["dU"].items():
+        ref = float(np.dot(w, dU))
+        errs[key] = abs(got[key] - ref) / abs(ref)
+    worst = max(errs.values())
+    print(f"{name}: energies {errU:.1e}, gradients {worst:.1e}", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert worst <= tol_g, errs
+
+
+def test_thickness_gradient_at_ties_is_the_forward_difference():
+    """Exact ties (tie_stack): the adjoint's derivative in an interface
+    position equals the forward finite difference of GPU solves (the
+    derivative for an increasing parameter), Richardson-extrapolated."""
+    from paper_2111_06893_gb300 import thermonoise
+    desc = tie_stack()
+    w = np.zeros(len(desc["materials"]))
+    w[1], w[2] = 1.0, 1.0  # the two layers at interface 2
+    ctx = thermonoise.setup(desc)
+    u, _ = ctx.solve(mode="f64", rtol=1e-15, raise_on_error=False)
+    J0 = float(np.dot(w, ctx.layer_energies(u)))
+    ctx._u = u
+    got, _ = gpu_gradient(ctx, desc, w)
+
+    def J(dz):
+        d = dict(desc)
+        z = list(desc["slab_z"])
+        z[2] += dz
+        d["slab_z"] = z
+        c = thermonoise.setup(d)
+        v, _ = c.solve(mode="f64", rtol=1e-15, raise_on_error=False)
+        return float(np.dot(w, c.layer_energies(v)))
+
+    t = desc["slab_z"][1] - desc["slab_z"][2]
+    h = 2e-4 * t
+    fwd = 2 * (J(h / 2) - J0) / (h / 2) - (J(h) - J0) / h
+    bwd = 2 * (J0 - J(-h / 2)) / (h / 2) - (J0 - J(-h)) / h
+    adj = got[json.dumps(["slab_z", 2])]
+    assert abs(adj - fwd) <= 1e-5 * abs(fwd), (adj, fwd, bwd)
+    # a real kink (the penalty term moves J only through the small jumps, so
+    # the two one-sided derivatives differ by ~1e-4 relative here), and the
+    # adjoint sits on the forward side of it
+    assert abs(bwd - fwd) > 10 * abs(adj - fwd), (adj, fwd, bwd)
 
 
 def test_gradient_matches_gpu_finite_differences_and_autograd():
@@ -98,7 +148,7 @@ def test_gradient_matches_gpu_finite_differences_and_autograd():
     mod = torch.tensor([thermonoise.iso_moduli(m["Y"], m["nu"]) if m["kind"] == "iso"
                         else (m["c11"], m["c12"], m["c44"]) for m in desc["materials"]],
                        dtype=torch.float64, requires_grad=True)
-    kw = {"mode": "f64", "rtol": 1e-13, "energy_rtol": 1e-13, "raise_on_error": False}
+    kw = {"mode": "f64", "rtol": 1e-15, "raise_on_error": False}
     U = EnergyFn.apply(slab_z, r0, mod, desc, kw)
     J = U[0] * 2.0 + U[1] + 0.5 * U[-1]
     J.backward()
@@ -108,7 +158,6 @@ def test_gradient_matches_gpu_finite_differences_and_autograd():
             V = EnergyFn.apply(sz, rr, mod, desc, kw)
         return float(V[0] * 2.0 + V[1] + 0.5 * V[-1])
 
-    # thickness of the first coating layer: moves slab_z[1:] ... only slab_z[1] here
     h = 1e-6
     e1 = torch.zeros_like(slab_z)
     e1[1] = h
@@ -121,8 +170,7 @@ def test_gradient_matches_gpu_finite_differences_and_autograd():
 def test_single_coating_full_size_gradient_matches_finite_differences():
     """Adjoint gradients on the 2.0 M DOF mirror against central differences
     of GPU solves, for parameters the energies depend on smoothly: the beam
-    width r0 and the moduli (slab positions of geometric substrate slabs sit
-    on kinks of min(h_int, h_ext))."""
+    width r0 and the moduli."""
     from paper_2111_06893_gb300 import thermonoise
     desc = W.single_coating()
     EnergyFn = thermonoise.energy_fn()
@@ -149,3 +197,34 @@ def test_single_coating_full_size_gradient_matches_finite_differences():
         dm[L, q] = hm
         fd = (Jval(r0.detach(), mod.detach() + dm) - Jval(r0.detach(), mod.detach() - dm)) / (2 * hm)
         assert abs(mod.grad[L, q].item() - fd) <= 1e-5 * abs(fd), (L, q, mod.grad[L, q].item(), fd)
+
+
+def test_crystalline_full_size_thickness_gradient_matches_forward_differences():
+    """The 40-layer cubic stack (8.0 M DOF): dJ/d(interface position) at
+    interface 20 (equal layers on both sides: ties of min(h_int, h_ext)
+    within rounding) against Richardson-extrapolated forward differences of
+    FP64 GPU solves, J = U_19 + U_20."""
+    from paper_2111_06893_gb300 import thermonoise
+    desc = W.crystalline_multilayer()
+    nl = len(desc["materials"])
+    w = np.zeros(nl)
+    w[19], w[20] = 1.0, 1.0
+    kw = {"mode": "f64", "rtol": 1e-15, "energy_rtol": 1e-13, "raise_on_error": False}
+    ctx = thermonoise.setup(desc)
+    u, _ = ctx.solve(**kw)
+    J0 = float(np.dot(w, ctx.layer_energies(u)))
+    g = ctx.energy_grad(u, w, mode="f64", rtol=1e-13, raise_on_error=False)
+    adj = g["slab_z"][20]
+
+    def J(dz):
+        d = dict(desc)
+        z = list(desc["slab_z"])
+        z[20] += dz
+        d["slab_z"] = z
+        c = thermonoise.setup(d)
+        v, _ = c.solve(**kw)
+        return float(np.dot(w, c.layer_energies(v)))
+
+    h = 1e-3 * 4e-4
+    fwd = 2 * (J(h / 2) - J0) / (h / 2) - (J(h) - J0) / h
+    assert abs(adj - fwd) <= 1e-4 * abs(fwd), (adj, fwd)
