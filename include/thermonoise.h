@@ -254,6 +254,23 @@ tn_status tn_solve(tn_ctx *ctx, const tn_solve_opts *opts, double *u_dev, tn_sol
  * n_layers doubles (coating layers top-down, substrate last).  Synchronises. */
 tn_status tn_layer_energies(tn_ctx *ctx, const double *u_dev, double *U_host);
 
+/* The layer energies of tn_layer_energies split by elastic modulus, for a
+ * noise PSD with a separate loss angle per modulus (Sec. 2.1: a material can
+ * carry different loss angles for its independent moduli; the split is this
+ * library's reading).  The energy density 1/2 S : Y : S of the cubic-aligned
+ * stiffness separates along its eigen-modes (T = tr S, D = sum_i S_ii^2,
+ * O = S_xy^2 + S_xz^2 + S_yz^2):
+ *   parts[3 L + 0]  dilatational  1/2 (c11 + 2 c12) / 3 T^2   (bulk modulus)
+ *   parts[3 L + 1]  tetragonal    1/2 (c11 - c12) (D - T^2 / 3)
+ *   parts[3 L + 2]  shear         1/2 4 c44 O
+ * each integrated like tn_layer_energies (element LGL nodes, unlifted
+ * strain); the three sum to U_L.  Isotropic layers: part 0 is the bulk
+ * energy K/2 int T^2, parts 1 + 2 the shear energy mu int S_dev : S_dev.
+ * One mesh or a batch (layers concatenated mirror by mirror).  u_dev: FP64
+ * field; parts_host: 3 * n_layers doubles.  Allocates a scratch of
+ * 3 * n_elements doubles for the call.  Synchronises. */
+tn_status tn_layer_energy_parts(tn_ctx *ctx, const double *u_dev, double *parts_host);
+
 /* Adjoint gradient of J = sum_i w_i U_i (energies of tn_layer_energies) for
  * the solution u of A u = b (caller-owned FP64 device buffer, e.g. from
  * tn_solve).  Because the weak-form operator is symmetric the adjoint

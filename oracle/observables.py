@@ -5,6 +5,8 @@
 * ``layer_energies``: U = -1/2 int S_ij T^ij dV with T = -Y S (Sec. 2.1),
   i.e. 1/2 int S : Y : S, evaluated per material layer with the element's own
   (unlifted) strain S = D_(k u_l) at its LGL nodes and LGL weights.
+* ``layer_energy_parts``: the same energies split by elastic modulus
+  (dilatational, tetragonal and shear strain subspaces of the stiffness).
 * ``noise_psd``: the fluctuation-dissipation relation, Eq. (thermalnoise),
   with the quasistatic loss of Eq. (wdiss) summed over layers.  Taken as a
   dissipated power (energy per cycle 2 pi U phi, times f) this reads
@@ -52,6 +54,50 @@ def layer_energies(op, u):
     for e in range(op.mesh.E):
         U[op.mesh.layer(e)] += element_energy(op, e, u)
     return U
+
+
+def _kelvin(S):
+    """Strain tensors (..., 3, 3) as Kelvin 6-vectors (S11, S22, S33,
+    sqrt2 S23, sqrt2 S13, sqrt2 S12), in which S : Y : S = s . C s."""
+    r2 = np.sqrt(2.0)
+    return np.stack([S[..., 0, 0], S[..., 1, 1], S[..., 2, 2], r2 * S[..., 1, 2], r2 * S[..., 0, 2],
+                     r2 * S[..., 0, 1]], axis=-1)
+
+
+def _kelvin_matrix(Y):
+    idx = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    sc = [1.0, 1.0, 1.0, np.sqrt(2.0), np.sqrt(2.0), np.sqrt(2.0)]
+    return np.array([[sc[a] * sc[b] * Y[idx[a] + idx[b]] for b in range(6)] for a in range(6)])
+
+
+def layer_energy_parts(op, u):
+    """[n_layers, 3]: the layer energies split by elastic modulus, for loss
+    angles attached to the independent moduli (Sec. 2.1 notes that a
+    material can carry several).  Reading: the energy density 1/2 s . C s of
+    the cubic-aligned (or isotropic) stiffness in Kelvin notation splits with
+    the orthogonal projectors onto its invariant subspaces -- dilatation
+    (1, 1, 1, 0, 0, 0)/sqrt3, the rest of the diagonal strains (tetragonal),
+    and the shear strains -- which C leaves invariant, so that the three
+    parts 1/2 s . P C P s add up to the energy."""
+    v0 = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0]) / np.sqrt(3.0)
+    P_dil = np.outer(v0, v0)
+    P_tet = np.diag([1.0, 1.0, 1.0, 0.0, 0.0, 0.0]) - P_dil
+    P_shr = np.diag([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    mesh = op.mesh
+    n, nloc = mesh.n, 3 * mesh.n
+    out = np.zeros((mesh.n_layers, 3))
+    for e in range(mesh.E):
+        ue = u[e * nloc:(e + 1) * nloc].reshape(3, n)
+        G = op.grad_matrices(e)
+        grad = np.stack([G[a] @ ue.T for a in range(3)], axis=1)
+        S = 0.5 * (grad + grad.transpose(0, 2, 1))
+        s6 = _kelvin(S)
+        C = _kelvin_matrix(op.Ye(e))
+        wJ = mesh.geometry(e)["wJ"]
+        for j, P in enumerate((P_dil, P_tet, P_shr)):
+            dens = np.einsum("pa,ab,pb->p", s6, P @ C @ P, s6)
+            out[mesh.layer(e), j] += 0.5 * np.sum(wJ * dens)
+    return out
 
 
 def noise_psd(U, phi, kB_T, f, F0):

@@ -133,6 +133,8 @@ struct tn_ctx {
   float apply_us[10][2] = {};
   // bounded device waits of the line solves (limit and timeout flag)
   TnWait *wctl = nullptr;
+  // counters of the PCG scalar steps folded into the grouped-line iteration
+  unsigned *fold_cnt = nullptr;
 };
 
 static void free_zline(tn_ctx *c) {
@@ -412,6 +414,7 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
 // the operator system with the grouped-line solve in place of the single lines
 static OpSys with_groups(OpSys s, const tn_ctx *c) {
   s.grouped = true;
+  s.fold_cnt = c->fold_cnt;
   s.zg = c->zgd;
   s.n_rz_parts = c->zgd.ngroups;
   s.zerr = c->wctl;
@@ -585,6 +588,8 @@ tn_status tn_create(tn_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->wctl, sizeof(TnWait));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->fold_cnt, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->fold_cnt, 0, 2 * sizeof(unsigned));
   if (e == cudaSuccess) {
     const TnWait w0{kDefaultWaitNs, 0, 0};
     e = cudaMemcpy(c->wctl, &w0, sizeof(w0), cudaMemcpyHostToDevice);
@@ -617,6 +622,7 @@ void tn_destroy(tn_ctx *c) {
   dfree(c->d_layer_c);
   dfree(c->d_layer_c32);
   dfree(c->wctl);
+  dfree(c->fold_cnt);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->sstream) cudaStreamDestroy(c->sstream);
@@ -1454,6 +1460,46 @@ tn_status tn_layer_energies(tn_ctx *c, const double *u, double *U_host) {
   CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
   if ((st = ensure_ws(c))) return st;
   CU_TRY(energies_host(c, u, U_host, c->stream), "energies");
+  return TN_OK;
+}
+
+tn_status tn_layer_energy_parts(tn_ctx *c, const double *u, double *parts_host) {
+  tn_status st = need_ready(c, false);
+  if (st) return st;
+  if ((st = check_buf(c, u, 8, "u"))) return st;
+  if (!parts_host) return fail(TN_EINVAL, "parts_host is null");
+  CU_TRY(cudaSetDevice(c->device), "cudaSetDevice");
+  const int n = is_batch(c) ? c->batch->n : 1;
+  size_t E = 0;
+  for (int i = 0; i < n; ++i) E += is_batch(c) ? (size_t)c->batch->inst[i].hm.E : (size_t)c->hm.E;
+  double *dev = nullptr;
+  CU_TRY(cudaMalloc((void **)&dev, sizeof(double) * 3 * E), "energy-parts scratch");
+  std::vector<double> h(3 * E);
+  cudaError_t e = cudaSuccess;
+  size_t eo = 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const DevMesh &dm = is_batch(c) ? c->batch->inst[i].dm : c->dm;
+    const long long off = is_batch(c) ? c->batch->inst[i].dof_off : 0;
+    e = tn_launch_energy_parts(dm, u + off, dev + 3 * eo, c->stream);
+    eo += dm.E;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dev, sizeof(double) * 3 * E, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "energy parts");
+  // per layer, slab by slab and column by column (fixed order)
+  const int nl = total_layers(c);
+  for (int l = 0; l < 3 * nl; ++l) parts_host[l] = 0.0;
+  eo = 0;
+  for (int i = 0; i < n; ++i) {
+    const tn::HostMesh &hm = is_batch(c) ? c->batch->inst[i].hm : c->hm;
+    const int lo = is_batch(c) ? c->batch->inst[i].layer_off : 0;
+    for (int el = 0; el < hm.E; ++el) {
+      const int L = lo + hm.slab_layer[el / hm.ncol];
+      for (int j = 0; j < 3; ++j) parts_host[3 * L + j] += h[3 * (eo + el) + j];
+    }
+    eo += hm.E;
+  }
   return TN_OK;
 }
 

@@ -874,11 +874,60 @@ __host__ __device__ constexpr int apply2_min_blocks() {
   return N == 3 ? 32 : (N == 4 ? 16 : (N == 5 ? 8 : (N == 6 ? 5 : (N == 7 ? 4 : (N == 8 ? 3 : 2)))));
 }
 
+// The alpha step of a PCG iteration folded into the operator apply: once
+// every CTA of the step has written its p . Ap partial, the last reduces
+// all partials in a fixed order (0 .. nparts - 1) and sets alpha = rz / pAp
+// (breakdown if pAp <= 0 or not finite).  A run that has finished skips the
+// apply and marks the iteration inactive.
+__device__ __forceinline__ bool fold_skip(const PcgFold &f) {
+  if (!f.s || !f.s->done) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) f.s->active = 0;
+  return true;
+}
+__device__ void fold_alpha(const PcgFold &f) {
+  const double *__restrict__ part = f.part;
+  __shared__ int last;
+  __shared__ double red[32];
+  __syncthreads();  // this CTA's partial is written
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(f.cnt, 1u) == (unsigned)(f.total - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < f.nparts; t += blockDim.x) acc += __ldcg(part + t);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pq = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pq += red[w];
+    tn_pcg_scalars *s = f.s;
+    s->active = 1;
+    s->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      s->breakdown = 1;
+      s->done = 1;
+      s->alpha = 0.0;
+    } else {
+      s->alpha = s->rz / pq;
+    }
+    *f.cnt = 0u;
+    __threadfence();
+  }
+}
+
 template <int N, typename T, int V>
 __global__ void __launch_bounds__(nthreads<N>(), (apply2_min_blocks<N, T, V>()))
-apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial) {
+apply2_kernel(const DevMesh m, int e0, const T *__restrict__ u, T *__restrict__ y, double *__restrict__ partial,
+              const PcgFold fold) {
+  if (fold_skip(fold)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   apply2_body<N, T>(m, e0 + blockIdx.x, u, y, partial ? partial + blockIdx.x : nullptr, smem_raw);
+  if (fold.s) fold_alpha(fold);
 }
 
 // a batch of meshes: CTA b works on element work[b].y of instance work[b].x
@@ -886,7 +935,8 @@ template <int N, typename T, int V>
 __global__ void __launch_bounds__(nthreads<N>(), (apply2_min_blocks<N, T, V>()))
 apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__ work,
                     const long long *__restrict__ dof_off, const T *__restrict__ u, T *__restrict__ y,
-                    double *__restrict__ partial) {
+                    double *__restrict__ partial, const PcgFold fold) {
+  if (fold_skip(fold)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) unsigned char sm_raw[sizeof(DevMesh)];
   DevMesh &sm = *reinterpret_cast<DevMesh *>(sm_raw);
@@ -895,6 +945,7 @@ apply2_batch_kernel(const DevMesh *__restrict__ meshes, const int2 *__restrict__
   __syncthreads();
   const long long off = dof_off[w.x];
   apply2_body<N, T>(sm, w.y, u + off, y + off, partial ? partial + blockIdx.x : nullptr, smem_raw);
+  if (fold.s) fold_alpha(fold);
 }
 
 // the dynamic shared-memory opt-in of a kernel, once per device
@@ -908,44 +959,49 @@ cudaError_t allow_smem(K kernel, size_t bytes, int &configured_device) {
   return err;
 }
 
+// fold / fold_part: the alpha step (fold_part: the partials of all the
+// step's launches, of which this launch writes `partial` onwards)
 template <int N, typename T, int V>
 cudaError_t launch_apply2_batch_v(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
-                                  const T *u, T *y, double *partial, cudaStream_t st) {
+                                  const T *u, T *y, double *partial, cudaStream_t st, const PcgFold &fold) {
   constexpr size_t sm = apply2_smem<N, T>();
   static int configured_device = -1;
   cudaError_t err = allow_smem(apply2_batch_kernel<N, T, V>, sm, configured_device);
   if (err != cudaSuccess) return err;
   if (nwork <= 0) return cudaSuccess;
-  apply2_batch_kernel<N, T, V><<<nwork, nthreads<N>(), sm, st>>>(meshes, work, dof_off, u, y, partial);
+  apply2_batch_kernel<N, T, V><<<nwork, nthreads<N>(), sm, st>>>(meshes, work, dof_off, u, y, partial, fold);
   return cudaGetLastError();
 }
 
 template <int N, typename T, int V>
-cudaError_t launch_apply2_v(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st) {
+cudaError_t launch_apply2_v(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st,
+                            const PcgFold &fold) {
   constexpr size_t sm = apply2_smem<N, T>();
   static int configured_device = -1;
   cudaError_t err = allow_smem(apply2_kernel<N, T, V>, sm, configured_device);
   if (err != cudaSuccess) return err;
-  apply2_kernel<N, T, V><<<m.E, nthreads<N>(), sm, st>>>(m, 0, u, y, partial);
+  apply2_kernel<N, T, V><<<m.E, nthreads<N>(), sm, st>>>(m, 0, u, y, partial, fold);
   return cudaGetLastError();
 }
 
 // variant 1 exists for FP32 only
 template <int N, typename T>
 cudaError_t launch_apply2_batch(const DevMesh *meshes, const int2 *work, int nwork, const long long *dof_off,
-                                const T *u, T *y, double *partial, cudaStream_t st, int var) {
+                                const T *u, T *y, double *partial, cudaStream_t st, int var,
+                                const PcgFold &fold = PcgFold()) {
   if constexpr (sizeof(T) == 4) {
-    if (var == 1) return launch_apply2_batch_v<N, T, 1>(meshes, work, nwork, dof_off, u, y, partial, st);
+    if (var == 1) return launch_apply2_batch_v<N, T, 1>(meshes, work, nwork, dof_off, u, y, partial, st, fold);
   }
-  return launch_apply2_batch_v<N, T, 0>(meshes, work, nwork, dof_off, u, y, partial, st);
+  return launch_apply2_batch_v<N, T, 0>(meshes, work, nwork, dof_off, u, y, partial, st, fold);
 }
 
 template <int N, typename T>
-cudaError_t launch_apply2(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var) {
+cudaError_t launch_apply2(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var,
+                          const PcgFold &fold = PcgFold()) {
   if constexpr (sizeof(T) == 4) {
-    if (var == 1) return launch_apply2_v<N, T, 1>(m, u, y, partial, st);
+    if (var == 1) return launch_apply2_v<N, T, 1>(m, u, y, partial, st, fold);
   }
-  return launch_apply2_v<N, T, 0>(m, u, y, partial, st);
+  return launch_apply2_v<N, T, 0>(m, u, y, partial, st, fold);
 }
 
 // time per launch (us) of both FP32 variants on one mesh (m1) or one degree
@@ -999,15 +1055,16 @@ cudaError_t launch_apply_range(const DevMesh &m, int s0, int s1, const TIO *u, T
 }
 
 template <typename T>
-cudaError_t launch_apply_t(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var) {
+cudaError_t launch_apply_t(const DevMesh &m, const T *u, T *y, double *partial, cudaStream_t st, int var,
+                           const PcgFold &fold) {
   switch (m.N) {
-    case 3: return launch_apply2<3, T>(m, u, y, partial, st, var);
-    case 4: return launch_apply2<4, T>(m, u, y, partial, st, var);
-    case 5: return launch_apply2<5, T>(m, u, y, partial, st, var);
-    case 6: return launch_apply2<6, T>(m, u, y, partial, st, var);
-    case 7: return launch_apply2<7, T>(m, u, y, partial, st, var);
-    case 8: return launch_apply2<8, T>(m, u, y, partial, st, var);
-    case 9: return launch_apply2<9, T>(m, u, y, partial, st, var);
+    case 3: return launch_apply2<3, T>(m, u, y, partial, st, var, fold);
+    case 4: return launch_apply2<4, T>(m, u, y, partial, st, var, fold);
+    case 5: return launch_apply2<5, T>(m, u, y, partial, st, var, fold);
+    case 6: return launch_apply2<6, T>(m, u, y, partial, st, var, fold);
+    case 7: return launch_apply2<7, T>(m, u, y, partial, st, var, fold);
+    case 8: return launch_apply2<8, T>(m, u, y, partial, st, var, fold);
+    case 9: return launch_apply2<9, T>(m, u, y, partial, st, var, fold);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1194,6 +1251,69 @@ energy_kernel(const DevMesh m, int e0, const double *__restrict__ u, const doubl
     double sum = 0.0;
     for (int ww = 0; ww < NT / 32; ++ww) sum += red[ww];
     elem[blockIdx.x] = sum;
+  }
+}
+
+// The layer energy split along the eigen-modes of the (cubic-aligned)
+// stiffness, for separate loss angles per modulus (Sec. 2.1): with
+// T = tr S, D = sum_i S_ii^2, O = S_xy^2 + S_xz^2 + S_yz^2,
+//   dilatational   1/2 (c11 + 2 c12) / 3 T^2
+//   tetragonal     1/2 (c11 - c12) (D - T^2 / 3)
+//   shear          1/2 4 c44 O
+// (they sum to 1/2 S : Y : S; isotropic: bulk K T^2 / 2 and shear
+// mu S_dev : S_dev = tetragonal + shear).  parts[3 e + j], element e.
+template <int N>
+__global__ void __launch_bounds__(nthreads<N>())
+energy_parts_kernel(const DevMesh m, const double *__restrict__ u, double *__restrict__ parts) {
+  constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
+  __shared__ double su[3 * n];
+  __shared__ double red[3][NT / 32];
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int s = e / m.ncol, c = e - s * m.ncol;
+  for (int t = tid; t < 3 * n; t += NT) su[t] = u[(size_t)e * 3 * n + t];
+  __syncthreads();
+  const double *cg = m.colgeo + (size_t)c * CG_NF * N2;
+  const int L = m.slab_layer[s];
+  const double c11 = m.layer_c[3 * L], c12 = m.layer_c[3 * L + 1], c44 = m.layer_c[3 * L + 2];
+  double pe[3] = {0.0, 0.0, 0.0};
+  if (tid < n) {
+    const int p = tid, i = p % N, j = (p / N) % N, k = p / N2;
+    double dxi[3], deta[3], dzeta[3];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double *v = su + cc * n;
+      double a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        a0 += Tab<double>::D(N, i, mm) * v[(k * N + j) * N + mm];
+        a1 += Tab<double>::D(N, j, mm) * v[(k * N + mm) * N + i];
+        a2 += Tab<double>::D(N, k, mm) * v[(mm * N + j) * N + i];
+      }
+      dxi[cc] = a0; deta[cc] = a1; dzeta[cc] = a2;
+    }
+    const int q = j * N + i;
+    const double dz = slab_dz<double>(m, s, k);
+    const Sym<double> S = strain<double>(dxi, deta, dzeta, cg[CG_IXX * N2 + q], cg[CG_IXY * N2 + q],
+                                         cg[CG_IEX * N2 + q], cg[CG_IEY * N2 + q], 1.0 / dz);
+    const double wJ = 0.5 * Tab<double>::w(N, i) * Tab<double>::w(N, j) * Tab<double>::w(N, k) *
+                      cg[CG_DET * N2 + q] * dz;
+    const double T = S.xx + S.yy + S.zz, D = S.xx * S.xx + S.yy * S.yy + S.zz * S.zz;
+    const double O = S.xy * S.xy + S.xz * S.xz + S.yz * S.yz;
+    pe[0] = wJ * (c11 + 2.0 * c12) / 3.0 * T * T;
+    pe[1] = wJ * (c11 - c12) * (D - T * T / 3.0);
+    pe[2] = wJ * 4.0 * c44 * O;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 3; ++jj) {
+    double v = pe[jj];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[jj][tid >> 5] = v;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double sum = 0.0;
+    for (int ww = 0; ww < NT / 32; ++ww) sum += red[tid][ww];
+    parts[(size_t)e * 3 + tid] = sum;
   }
 }
 
@@ -1389,11 +1509,14 @@ cudaError_t launch_energy_dual_n(const DevMesh &m, int s0, int s1, const double 
 }  // namespace
 
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
-                            double *partial, int var, cudaStream_t st) {
+                            double *partial, int var, cudaStream_t st, const PcgFold *fold) {
+  const PcgFold f = fold ? *fold : PcgFold();
   if (precision == TN_F64)
-    return launch_apply_t<double>(m, (const double *)u, (double *)y, partial, st, 0);
-  return launch_apply_t<float>(m, (const float *)u, (float *)y, partial, st, var);
+    return launch_apply_t<double>(m, (const double *)u, (double *)y, partial, st, 0, f);
+  return launch_apply_t<float>(m, (const float *)u, (float *)y, partial, st, var, f);
 }
+
+int tn_apply_ctas(const DevMesh *m, int nwork) { return m ? m->E : nwork; }
 
 cudaError_t tn_tune_apply(const DevMesh *m1, int N, const DevMesh *meshes, const int2 *work, int nwork,
                           const long long *dof_off, const float *u, float *y, cudaStream_t st, float us[2]) {
@@ -1449,6 +1572,16 @@ cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem, do
   return cudaGetLastError();
 }
 
+cudaError_t tn_launch_energy_parts(const DevMesh &m, const double *u, double *parts, cudaStream_t st) {
+  switch (m.N) {
+#define TN_CASE(NN) \
+    case NN: energy_parts_kernel<NN><<<m.E, nthreads<NN>(), 0, st>>>(m, u, parts); return cudaGetLastError();
+    TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 #define TN_DISPATCH_N(...)                  \
   switch (m.N) {                            \
     case 3: { constexpr int NN = 3; __VA_ARGS__; } \
@@ -1484,15 +1617,16 @@ cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const doub
 
 cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
                                   const long long *dof_off, const void *u, void *y, double *partial,
-                                  int var, cudaStream_t st) {
+                                  int var, cudaStream_t st, const PcgFold *fold) {
+  const PcgFold f = fold ? *fold : PcgFold();
   switch (N) {
 #define TN_CASE(NN)                                                                                    \
   case NN:                                                                                            \
     return precision == TN_F64                                                                        \
                ? launch_apply2_batch<NN, double>(meshes, work, nwork, dof_off, (const double *)u,    \
-                                                 (double *)y, partial, st, 0)                         \
+                                                 (double *)y, partial, st, 0, f)                      \
                : launch_apply2_batch<NN, float>(meshes, work, nwork, dof_off, (const float *)u,      \
-                                                (float *)y, partial, st, var);
+                                                (float *)y, partial, st, var, f);
     TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
     default: return cudaErrorInvalidValue;

@@ -1136,6 +1136,48 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   }
 }
 
+// The beta step of a PCG iteration folded into the grouped-line solve: once
+// every CTA of all the step's launches has written its groups' r.z and r.r
+// partials, the last reduces them in a fixed order (group 0 .. ngroups - 1)
+// and updates beta and the stopping test.
+__device__ void fold_beta(const PcgFold &f) {
+  __shared__ int last;
+  __shared__ double red[2][kZgThreads / 32];
+  __syncthreads();  // every slot of this CTA has written its partials
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(f.cnt, 1u) == (unsigned)(f.total - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double rz = 0.0, rr = 0.0;
+  for (int t = threadIdx.x; t < f.nparts; t += blockDim.x) {
+    rz += __ldcg(f.part + t);
+    rr += __ldcg(f.part2 + t);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz += __shfl_xor_sync(0xffffffffu, rz, o);
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = rz;
+    red[1][threadIdx.x >> 5] = rr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kZgThreads / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    pcg_finish_beta(f.s, a, b);
+    *f.cnt = 0u;
+    __threadfence();
+  }
+}
+
 // packs [pk0, pk0 + npk) of one degree; CTAs take packs from queue[0]
 // (largest first); the last CTA to finish resets queue[0..1] for the next
 // launch.  One mesh (ginst == nullptr) or a batch (per group: its mirror's
@@ -1148,7 +1190,7 @@ zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevM
                      int *__restrict__ queue, const T *__restrict__ fac, T *__restrict__ r,
                      const T *__restrict__ q, T *__restrict__ z, const double *__restrict__ alpha,
                      double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
-                     TnWait *__restrict__ err) {
+                     TnWait *__restrict__ err, const PcgFold fold) {
   if (done && *done) return;
   constexpr int SW = zg_stage_per_warp<N, T>();
   extern __shared__ __align__(16) unsigned char zsm[];
@@ -1227,6 +1269,7 @@ zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevM
       __threadfence();
     }
   }
+  if (fold.s) fold_beta(fold);
 }
 
 template <int N>
@@ -1318,15 +1361,16 @@ cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, int inst, cons
   return err;
 }
 
+// persistent: as many CTAs as fit at once, never more than packs.  grid == 0:
+// only compute the grid into *grid_out; else launch with it.
 template <int N, typename T, bool UPD>
 cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const void *fac, void *r, const void *q,
                             void *z, const double *alpha, double *prz, double *prr, const int *done, TnWait *zerr,
-                            cudaStream_t st) {
+                            cudaStream_t st, const PcgFold &fold, int *grid_out) {
   constexpr size_t sm = zg_smem<N, T>();
   auto kern = zgroup_packed_kernel<N, T, UPD>;
   cudaError_t err = zline_smem_optin(kern, sm);
   if (err != cudaSuccess) return err;
-  // persistent: as many CTAs as fit at once, never more than packs
   static int per_sm[64] = {0};
   int dev = 0;
   err = cudaGetDevice(&dev);
@@ -1340,21 +1384,29 @@ cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const 
   }
   int grid = per_sm[dev] * tn_sm_count();
   grid = grid < gd.pk_n[k] ? grid : gd.pk_n[k];
+  if (grid_out) {
+    *grid_out = grid;
+    return cudaSuccess;
+  }
   kern<<<grid, kZgThreads, sm, st>>>(m, gd.inst, gd.meshes, gd.dof_off, gd.lines, gd.fac_off, gd.packs,
                                      gd.pk_start[k], gd.pk_n[k], gd.queue + 2 * k, (const T *)fac, (T *)r,
-                                     (const T *)q, (T *)z, alpha, prz, prr, done, zerr);
+                                     (const T *)q, (T *)z, alpha, prz, prr, done, zerr, fold);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int k, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *prz, double *prr,
-                            const int *done, TnWait *zerr, cudaStream_t st) {
+                            const int *done, TnWait *zerr, cudaStream_t st, const PcgFold &fold, int *grid_out) {
   if (prec == TN_F64)
-    return q ? zgroup_launch_t<N, double, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-             : zgroup_launch_t<N, double, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st);
-  return q ? zgroup_launch_t<N, float, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st)
-           : zgroup_launch_t<N, float, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st);
+    return q ? zgroup_launch_t<N, double, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
+                                                grid_out)
+             : zgroup_launch_t<N, double, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
+                                                 grid_out);
+  return q ? zgroup_launch_t<N, float, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
+                                             grid_out)
+           : zgroup_launch_t<N, float, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
+                                              grid_out);
 }
 
 }  // namespace
@@ -1509,9 +1561,31 @@ cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, con
 // inside a capture)
 cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                            const int *done, TnWait *zerr, cudaStream_t st) {
+                            const int *done, TnWait *zerr, cudaStream_t st, const PcgFold *fold_in) {
   const DevMesh one = m ? *m : DevMesh{};
   cudaError_t err = cudaSuccess;
+  PcgFold fold = fold_in ? *fold_in : PcgFold();
+  if (fold.s) {  // the grids of every launch, for the last-CTA count
+    fold.total = 0;
+    fold.nparts = gd.ngroups;
+    fold.part = part_rz;
+    fold.part2 = part_rr;
+    for (int k = 0; k < gd.npk && err == cudaSuccess; ++k) {
+      int g = 0;
+      switch (gd.pk_N[k]) {
+#define TN_CASE(NN)                                                                                              \
+        case NN:                                                                                                \
+          err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st, fold, \
+                                    &g);                                                                        \
+          break;
+        TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
+#undef TN_CASE
+        default: err = cudaErrorInvalidValue;
+      }
+      fold.total += g;
+    }
+    if (err != cudaSuccess) return err;
+  }
   if (gd.npk > 1) err = cudaEventRecord(gd.fork, st);
   bool used[kZgSide] = {false};
   for (int k = 0; k < gd.npk && err == cudaSuccess; ++k) {
@@ -1528,7 +1602,8 @@ cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, con
     switch (gd.pk_N[k]) {
 #define TN_CASE(NN)                                                                                        \
       case NN:                                                                                            \
-        err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, sk); \
+        err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, sk, fold, \
+                                  nullptr);                                                                 \
         break;
       TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE

@@ -300,18 +300,6 @@ __global__ void k_upcast(size_t n, const float *__restrict__ d, double scale, do
 }
 
 // ---- variants for a preconditioner applied by a separate kernel (z-line)
-__device__ void finish_beta(tn_pcg_scalars *s, double rz, double rr) {
-  s->iters += 1;
-  s->rr = rr;
-  if (!isfinite(rr) || !isfinite(rz)) {
-    s->breakdown = 1;
-    s->done = 1;
-    return;
-  }
-  s->beta = rz / s->rz;
-  s->rz = rz;
-  if (rr <= s->tol2 || s->iters >= s->max_iters) s->done = 1;
-}
 
 __global__ void k_beta_split(tn_pcg_scalars *s, const double *rzp, int nrz, const double *rrp, int nrr) {
   if (s->done) return;
@@ -319,7 +307,7 @@ __global__ void k_beta_split(tn_pcg_scalars *s, const double *rzp, int nrz, cons
   for (int t = threadIdx.x; t < nrz; t += blockDim.x) rz += rzp[t];
   for (int t = threadIdx.x; t < nrr; t += blockDim.x) rr += rrp[t];
   block_sum2(rz, rr);
-  if (threadIdx.x == 0) finish_beta(s, rz, rr);
+  if (threadIdx.x == 0) pcg_finish_beta(s, rz, rr);
 }
 
 // x += alpha p (the iteration's solution update, deferred to here so that
@@ -419,6 +407,23 @@ static cudaError_t pcg_iteration(const OpSys &sys, int prec, size_t n, PcgVector
 template <typename T>
 static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                        double *part_elem, double *part_red, cudaStream_t st) {
+  if (sys.grouped && sys.fold_cnt) {
+    // three launches: the apply with the alpha step, the grouped-line solve
+    // with the residual update and the beta step, the direction update
+    PcgFold fa;
+    fa.s = s;
+    fa.cnt = sys.fold_cnt;
+    fa.total = sys.n_apply_parts;  // one CTA per element
+    fa.nparts = sys.n_apply_parts;
+    fa.part = part_elem;
+    TN_CU(sys.apply(prec, v.p, v.q, part_elem, st, &fa));
+    PcgFold fb;
+    fb.s = s;
+    fb.cnt = sys.fold_cnt + 1;
+    TN_CU(sys.zsolve(prec, v.zfac, v.r, v.q, v.z, &s->alpha, v.part_rz, &s->done, st, &fb));
+    k_pupdate_x<T><<<red_blocks(), kRedThreads, 0, st>>>(s, n, (T *)v.x, (T *)v.p, (const T *)v.z);
+    return cudaGetLastError();
+  }
   TN_CU(sys.apply(prec, v.p, v.q, part_elem, st));
   k_alpha<<<1, 1024, 0, st>>>(s, part_elem, sys.n_apply_parts);
   TN_CU(cudaGetLastError());
@@ -465,6 +470,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   TN_CU(cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st));
   TN_CU(cudaStreamSynchronize(st));
   if (s_host->done) return cudaSuccess;
+  if (zl && sys.grouped && sys.fold_cnt) TN_CU(cudaMemsetAsync(sys.fold_cnt, 0, 2 * sizeof(unsigned), st));
 
   // one graph of `chunk` iterations, cached while the run's buffers are unchanged
   struct Key {
@@ -514,7 +520,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   double best = INFINITY;
   int stall = 0;
   for (;;) {
-    g_launches += 5LL * chunk;
+    g_launches += (zl && sys.grouped && sys.fold_cnt ? 3LL : 5LL) * chunk;
     err = cudaGraphLaunch(exec, st);
     if (err != cudaSuccess) break;
     err = cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st);
@@ -604,20 +610,21 @@ int reduction_blocks() { return red_blocks(); }
 
 }  // namespace tn
 
-cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const {
-  if (m) return tn_launch_apply(*m, prec, u, y, part, mvar, st);
+cudaError_t OpSys::apply(int prec, const void *u, void *y, double *part, cudaStream_t st,
+                         const PcgFold *fold) const {
+  if (m) return tn_launch_apply(*m, prec, u, y, part, mvar, st, fold);
   for (int g = 0; g < ngroups; ++g) {
     cudaError_t e = tn_launch_apply_batch(gN[g], prec, meshes, gwork[g], gcount[g], dof_off, u, y,
-                                          part ? part + gpart_off[g] : nullptr, gvar[g], st);
+                                          part ? part + gpart_off[g] : nullptr, gvar[g], st, fold);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 cudaError_t OpSys::zsolve(int prec, const void *fac, void *r, const void *q, void *z, const double *alpha,
-                          double *part, const int *done, cudaStream_t st) const {
+                          double *part, const int *done, cudaStream_t st, const PcgFold *fold) const {
   double *prr = part ? part + n_rz_parts : nullptr;
-  if (grouped) return tn_zgroup_solve(m, zg, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
+  if (grouped) return tn_zgroup_solve(m, zg, prec, fac, r, q, z, alpha, part, prr, done, zerr, st, fold);
   if (m) return tn_zline_solve(*m, prec, fac, r, q, z, alpha, part, prr, done, zerr, st);
   for (int g = 0; g < ngroups; ++g) {
     cudaError_t e = tn_zline_solve_batch(gN[g], prec, meshes, gline[g], glines[g], fac_off, dof_off, fac, r, q, z,

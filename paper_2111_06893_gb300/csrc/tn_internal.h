@@ -67,6 +67,44 @@ struct TnWait {
 };
 constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // 1 s
 
+// device-resident Krylov scalars of one PCG run
+struct tn_pcg_scalars {
+  double rz, rr, rr0, pq, alpha, beta, tol2;
+  int iters, max_iters, done, breakdown;
+  int active;  // the current iteration ran (set by the alpha step)
+};
+
+// A PCG scalar step folded into the kernel that produces its partial sums:
+// every CTA of the step's launches counts itself on cnt once its partial is
+// written; the last one reduces the nparts partials in a fixed order,
+// updates the scalars and resets cnt.  s == nullptr: no fold.
+struct PcgFold {
+  tn_pcg_scalars *s = nullptr;
+  unsigned *cnt = nullptr;
+  int total = 0;              // CTAs of all launches of the step
+  int nparts = 0;             // partial sums to reduce
+  const double *part = nullptr;   // the first of them (the second sum's follow at part2)
+  const double *part2 = nullptr;
+};
+
+#ifdef __CUDACC__
+// the beta step of a PCG iteration from the new r.z and r.r: beta, the
+// stopping test (rr <= tol2 or the iteration limit), breakdown if either
+// sum is not finite
+__device__ inline void pcg_finish_beta(tn_pcg_scalars *s, double rz, double rr) {
+  s->iters += 1;
+  s->rr = rr;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    s->breakdown = 1;
+    s->done = 1;
+    return;
+  }
+  s->beta = rz / s->rz;
+  s->rz = rz;
+  if (rr <= s->tol2 || s->iters >= s->max_iters) s->done = 1;
+}
+#endif
+
 // forward-mode dual number (value, derivative along one direction)
 struct Dual {
   double v, d;
@@ -135,16 +173,22 @@ cudaError_t tn_launch_rhs_dr0(const DevMesh &m, double r0, double F0, const doub
 // var: occupancy variant of the FP32 kernel (0 or 1, same results)
 cudaError_t tn_launch_apply_batch(int N, int precision, const DevMesh *meshes, const int2 *work, int nwork,
                                   const long long *dof_off, const void *u, void *y, double *partial,
-                                  int var, cudaStream_t st);
+                                  int var, cudaStream_t st, const PcgFold *fold = nullptr);
 // us[v]: time per launch of FP32 variant v on one mesh (m1) or on one degree
 // group of a batch (m1 = nullptr); y is overwritten
 cudaError_t tn_tune_apply(const DevMesh *m1, int N, const DevMesh *meshes, const int2 *work, int nwork,
                           const long long *dof_off, const float *u, float *y, cudaStream_t st, float us[2]);
 cudaError_t tn_launch_energy_batch(int N, const DevMesh *meshes, const int2 *work, int nwork,
                                    const long long *dof_off, const double *u, double *out, cudaStream_t st);
+// fold (optional): the alpha step of a PCG iteration (partial = p . Ap per CTA)
 cudaError_t tn_launch_apply(const DevMesh &m, int precision, const void *u, void *y,
-                            double *partial, int var, cudaStream_t st);
+                            double *partial, int var, cudaStream_t st, const PcgFold *fold = nullptr);
+// CTAs one apply launches (one mesh, or one degree group of a batch)
+int tn_apply_ctas(const DevMesh *m, int nwork);
 cudaError_t tn_launch_rhs(const DevMesh &m, double r0, double F0, double *b, cudaStream_t st);
 cudaError_t tn_launch_diag(const DevMesh &m, double *d, cudaStream_t st);
 cudaError_t tn_launch_energy(const DevMesh &m, const double *u, double *elem_energy,
                              double *layer_energy, cudaStream_t st);
+// parts[3 e + j]: the dilatational, tetragonal and shear parts of element e's
+// energy (one mesh, FP64)
+cudaError_t tn_launch_energy_parts(const DevMesh &m, const double *u, double *parts, cudaStream_t st);

@@ -75,6 +75,8 @@ cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, con
                             double *fac64, int *status, cudaStream_t st);
 // as tn_zline_solve, over the groups (m: the mesh, nullptr for a batch);
 // partial sums: one per group
+// fold (optional): the beta step of a PCG iteration (s and cnt; the rest is
+// filled in here)
 cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
                             const void *q, void *z, const double *alpha, double *part_rz, double *part_rr,
-                            const int *done, TnWait *zerr, cudaStream_t st);
+                            const int *done, TnWait *zerr, cudaStream_t st, const PcgFold *fold = nullptr);

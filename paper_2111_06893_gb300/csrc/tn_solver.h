@@ -7,12 +7,6 @@
 #include "tn_internal.h"
 #include "tn_precond.h"
 
-// device-resident Krylov scalars of one PCG run
-struct tn_pcg_scalars {
-  double rz, rr, rr0, pq, alpha, beta, tol2;
-  int iters, max_iters, done, breakdown;
-  int active;  // the current iteration ran (set by the alpha step)
-};
 
 // the operator and preconditioner of a solve: one mesh, or a batch of meshes
 // grouped by polynomial degree (one launch per group)
@@ -33,13 +27,16 @@ struct OpSys {
   int n_apply_parts = 0;  // partial sums written by one apply
   int n_rz_parts = 0;     // partial sums of r.z written by one z-line solve (r.r: as many, after them)
   TnWait *zerr = nullptr; // wait limit of the line solves; flag set by one whose staging wait ran out
+  unsigned *fold_cnt = nullptr;  // grouped lines: 2 counters of the alpha / beta steps folded into
+                                 // the apply and the line solve (nullptr: separate scalar kernels)
   bool grouped = false;   // grouped lines (zg) instead of single lines
   ZGroupDev zg;
-  cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st) const;
+  cudaError_t apply(int prec, const void *u, void *y, double *part, cudaStream_t st,
+                    const PcgFold *fold = nullptr) const;
   // z = M^{-1} r; q != nullptr: first r <- r - (*alpha) q.  part: n_rz_parts
   // partial r.z, then n_rz_parts partial r.r
   cudaError_t zsolve(int prec, const void *fac, void *r, const void *q, void *z, const double *alpha,
-                     double *part, const int *done, cudaStream_t st) const;
+                     double *part, const int *done, cudaStream_t st, const PcgFold *fold = nullptr) const;
 };
 
 // vectors of one PCG run, all of the run's precision

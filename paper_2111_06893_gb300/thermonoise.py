@@ -31,7 +31,8 @@ SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof
            "tn_set_materials", "tn_set_beam", "tn_apply_operator", "tn_rhs", "tn_diagonal",
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
            "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes",
-           "tn_apply_tuning", "tn_set_apply_variant", "tn_iso_moduli", "tn_fma_peak"]
+           "tn_apply_tuning", "tn_set_apply_variant", "tn_iso_moduli", "tn_fma_peak",
+           "tn_layer_energy_parts"]
 
 
 class MeshDesc(C.Structure):
@@ -106,6 +107,7 @@ def load():
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
                                      C.POINTER(SolveReport)]),
         "tn_layer_energies_noalloc": (C.c_int, [vp, vp, dp]),
+        "tn_layer_energy_parts": (C.c_int, [vp, vp, dp]),
         "tn_batch_create": (C.c_int, [vp, C.c_int]),
         "tn_batch_set": (C.c_int, [vp, C.c_int, C.POINTER(MeshDesc), C.c_int, C.POINTER(Material),
                                    C.c_double, C.c_double]),
@@ -385,6 +387,16 @@ class Context:
         _check(load().tn_layer_energies(self._h, C.c_void_p(u.data_ptr()),
                                         U.ctypes.data_as(C.POINTER(C.c_double))))
         return U
+
+    def layer_energy_parts(self, u):
+        """[n_layers, 3]: dilatational, tetragonal and shear parts of every
+        layer energy (tn_layer_energy_parts)."""
+        self._check_tensor(u, self._torch.float64, "u")
+        n = len(self.desc["materials"])
+        P = np.zeros(3 * n)
+        _check(load().tn_layer_energy_parts(self._h, C.c_void_p(u.data_ptr()),
+                                            P.ctypes.data_as(C.POINTER(C.c_double))))
+        return P.reshape(n, 3)
 
 
 def noise_psd(U, phi, kB_T, f, F0):

@@ -471,3 +471,42 @@ def test_tie_of_face_sizes_takes_the_forward_derivative(dz_bottom):
     bwd = 2 * (U0 - U(-h / 2)) / (h / 2) - (U0 - U(-h)) / h
     assert abs(cs - fwd) < 1e-6 * abs(fwd), (cs, fwd)
     assert abs(bwd - fwd) > 1e-3 * abs(fwd), (bwd, fwd)
+
+
+# ------------------------------------------------- energy split by modulus
+
+def _one_element_box(material):
+    return W.box([-0.5, 0.7], [-0.4, 0.9], [0.0, -1.1], 2, material, penalty_C=3.0,
+                 bc_side="free", bc_bottom="free")
+
+
+@pytest.mark.parametrize("material", [W.CRYSTAL_A, W.COATING_HIGH])
+def test_energy_parts_of_pure_strain_modes(material):
+    """Linear fields with a pure dilatational, tetragonal or shear strain on
+    one element: the parts are the closed forms 3/2 (c11 + 2 c12) V,
+    (c11 - c12) V and 2 c44 V, the other parts vanish."""
+    desc = _one_element_box(material)
+    mesh = Mesh(desc)
+    op = Operator(mesh)
+    x = np.array([mesh.geometry(0)["xyz"][:, a] for a in range(3)])  # node coordinates
+    V = 1.2 * 1.3 * 1.1
+    Y = materials.tensor(material)
+    c11, c12, c44 = Y[0, 0, 0, 0], Y[0, 0, 1, 1], Y[0, 1, 0, 1]
+    fields = {0: (x[0], x[1], x[2]), 1: (x[0], -x[1], 0 * x[2]), 2: (x[1], x[0], 0 * x[2])}
+    expect = {0: 1.5 * (c11 + 2 * c12) * V, 1: (c11 - c12) * V, 2: 2 * c44 * V}
+    for mode, comps in fields.items():
+        u = np.concatenate([np.asarray(c, dtype=float) for c in comps])
+        P = ob.layer_energy_parts(op, u)[0]
+        for j in range(3):
+            ref = expect[mode] if j == mode else 0.0
+            assert abs(P[j] - ref) <= 1e-12 * expect[mode], (mode, j, P[j], ref)
+
+
+def test_energy_parts_add_up_to_layer_energies():
+    desc = W.cylinder(10.0, 10.0, [0.05, 0.02], [W.CRYSTAL_A, W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 2)
+    op = Operator(Mesh(desc))
+    u = W.random_field(desc, 3)
+    P = ob.layer_energy_parts(op, u)
+    U = ob.layer_energies(op, u)
+    assert np.all(P >= -1e-12 * U[:, None])
+    assert np.max(np.abs(P.sum(axis=1) - U) / U) < 1e-13

@@ -393,3 +393,35 @@ def test_invalid_arguments_are_rejected_before_launch():
     with pytest.raises(thermonoise.ThermonoiseError, match="TN_ESTATE"):
         c2 = thermonoise.Context()
         c2.apply_operator(u)
+
+
+@pytest.mark.parametrize("name", ["box_layers_p4", "cyl_small_p4_k2", "cyl_thin_p5"])
+def test_energy_parts_match_oracle_on_random_field(name):
+    """tn_layer_energy_parts against the oracle's projector split (dilatational,
+    tetragonal, shear) of every layer, and the parts add up to the energies."""
+    from paper_2111_06893_gb300 import thermonoise
+    desc = CASES[name]()
+    op = Operator(Mesh(desc))
+    u = W.random_field(desc, 5)
+    Po = ob.layer_energy_parts(op, u)
+    ctx = thermonoise.setup(desc)
+    ut = torch.tensor(u, dtype=torch.float64, device="cuda")
+    P = ctx.layer_energy_parts(ut)
+    U = ctx.layer_energies(ut)
+    scale = U[:, None]
+    assert np.max(np.abs(P - Po) / scale) < 1e-12, (P, Po)
+    assert np.max(np.abs(P.sum(axis=1) - U) / U) < 1e-13
+
+
+def test_energy_parts_of_a_batch_match_single_mirrors():
+    from paper_2111_06893_gb300 import thermonoise
+    descs = [CASES["box_layers_p4"](), CASES["cyl_small_p4_k1"](), CASES["box_tiny_p2"]()]
+    bc = thermonoise.Context().build_batch(descs)
+    u = torch.tensor(np.random.default_rng(7).uniform(-1, 1, size=int(bc.dof_off[-1])), dtype=torch.float64,
+                     device="cuda")
+    P = bc.layer_energy_parts(u)
+    lo = bc.layer_off
+    for i, d in enumerate(descs):
+        sc = thermonoise.setup(d)
+        Pi = sc.layer_energy_parts(u[bc.dof_off[i]:bc.dof_off[i + 1]].clone())
+        assert np.array_equal(P[lo[i]:lo[i + 1]], Pi), i
