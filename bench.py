@@ -212,6 +212,60 @@ def oracle_direct_solve_s():
     return time.perf_counter() - t0
 
 
+def voigt_isotropic(c):
+    """Effective isotropic moduli of a cubic crystal (Voigt average, the
+    amorphous model the approximate formula assumes): K = (c11 + 2 c12)/3,
+    G = (c11 - c12 + 3 c44)/5, then Y = 9 K G / (3 K + G),
+    nu = (3 K - 2 G) / (2 (3 K + G))."""
+    K = (c["c11"] + 2 * c["c12"]) / 3.0
+    G = (c["c11"] - c["c12"] + 3 * c["c44"]) / 5.0
+    return W.iso(9 * K * G / (3 * K + G), (3 * K - 2 * G) / (2 * (3 * K + G)))
+
+
+def finite_size_study(device):
+    """The analogue of Sec. 3.2 on synthetic parameters: the coating noise
+    of a single coating on a finite cylinder (R = H), solved, against the
+    approximate thin-coating / semi-infinite formula Eq. (approx_analytic),
+    across R / r0 and d / r0; and the crystalline correction, a cubic
+    coating against its effective isotropic (Voigt) model.  Near the beam
+    the mesh is the same for every R (central square of half-width 2 r0,
+    inner wedges to 4 r0, k = 3), so that the ratio isolates the size
+    effect; p-refinement at one mirror shows the discretization error."""
+    from paper_2111_06893_gb300 import thermonoise
+    kT, f, phi = KB_T, FREQ, 4e-4
+    crystal = W.CRYSTAL_A
+    iso_eff = voigt_isotropic(crystal)
+
+    def run(R, d, coat, degree=6, k=3):
+        desc = W.cylinder(R, R, [d], [coat], W.FUSED_SILICA, k, degree, 23, a=2.0, R1=4.0)
+        ctx = thermonoise.setup(desc, device=device)
+        u, rep = ctx.solve(mode="mixed", rtol=1e-13, energy_rtol=1e-11, raise_on_error=False)
+        U = ctx.layer_energies(u)
+        return U[0], rep, W.n_dof(desc)
+
+    for R in (5.0, 10.0, 20.0):
+        for d in (0.005, 0.01, 0.02, 0.04):
+            t0 = time.perf_counter()
+            Uc, rep, ndof = run(R, d, iso_eff)
+            S_num = thermonoise.noise_psd(np.array([Uc]), np.array([phi]), kT, f, 1.0)
+            S_an = thermonoise.thin_coating_psd(kT, f, 1.0, d, W.FUSED_SILICA, iso_eff, phi)
+            Ux, repx, _ = run(R, d, crystal)
+            print(json.dumps({"study": "finite_size", "R_over_r0": R, "d_over_r0": d, "degree": 6, "ndof": ndof,
+                              "S_numerical_over_approx": S_num / S_an,
+                              "finite_size_effect_pct": 100 * (S_num / S_an - 1),
+                              "crystalline_effect_pct": 100 * (Ux / Uc - 1),
+                              "rel_residual": [rep["rel_residual"], repx["rel_residual"]],
+                              "seconds": time.perf_counter() - t0}), flush=True)
+    for degree in (5, 6, 7):
+        Uc, rep, ndof = run(10.0, 0.02, iso_eff, degree=degree)
+        S_num = thermonoise.noise_psd(np.array([Uc]), np.array([phi]), kT, f, 1.0)
+        S_an = thermonoise.thin_coating_psd(kT, f, 1.0, 0.02, W.FUSED_SILICA, iso_eff, phi)
+        Ux, _, _ = run(10.0, 0.02, crystal, degree=degree)
+        print(json.dumps({"study": "finite_size_p_refinement", "R_over_r0": 10.0, "d_over_r0": 0.02,
+                          "degree": degree, "ndof": ndof, "finite_size_effect_pct": 100 * (S_num / S_an - 1),
+                          "crystalline_effect_pct": 100 * (Ux / Uc - 1)}), flush=True)
+
+
 def bench_config(args, descs, world):
     """The `config` of the JSON line, the same for both arms."""
     batched = len(descs) > 1 or args.workload == "design_sweep"
@@ -286,8 +340,9 @@ def main():
     ap.add_argument("--no-reference", action="store_true",
                     help="skip the FP64 reference solve (energy errors are then not reported)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
-    ap.add_argument("--mode", default="step", choices=["step", "apply"],
-                    help="apply: only time the FP32 / FP64 operator applies (for profiling)")
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "finite_size"],
+                    help="apply: only time the FP32 / FP64 operator applies (for profiling); "
+                         "finite_size: the finite-size and crystalline study (one JSON line per mirror)")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--cpu-budget-s", type=float, default=8.0)
     ap.add_argument("--grad", action="store_true",
@@ -330,6 +385,11 @@ def main():
     dof_w = [W.n_dof(d) for d in descs]
     flops_dof = sum(fp32_apply_flops_per_dof(d["degree"] + 1) * w for d, w in zip(descs, dof_w)) / sum(dof_w)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.mode == "finite_size":
+        if rank == 0:
+            finite_size_study(local)
+        return
 
     if args.mode == "apply":
         x32 = torch.rand(ndof, dtype=torch.float32, device=dev)

@@ -338,6 +338,20 @@ tn_status tn_batch_energy_grad(tn_ctx *ctx, const tn_solve_opts *opts, const dou
  * Synchronises the context's stream. */
 tn_status tn_layer_energies_noalloc(tn_ctx *ctx, const double *u_dev, double *U_host);
 
+/* The approximate coating thermal noise of a thin isotropic coating on a
+ * semi-infinite isotropic mirror, Eq. (approx_analytic) (coating
+ * contribution; valid for d << r0, r0 << R): the reference of the
+ * finite-size study (Sec. 3.2), to which the solved
+ * S_q = 4 kB_T phi_c U_coat / (pi f F0^2) (tn_noise_psd) is compared.
+ *   S = kB_T / (pi^2 f) (1 - nus^2) / (r0 Ys) (d / r0)
+ *       phi_c / (Ys Yc (1 - nuc^2)(1 - nus^2))
+ *       [Yc^2 (1 + nus)^2 (1 - 2 nus)^2 + Ys^2 (1 + nuc)^2 (1 - 2 nuc)]
+ * Substrate (Ys, nus), coating (Yc, nuc), thickness d, beam width r0, loss
+ * angle phi_c.  Host only; TN_EINVAL for non-positive scales or
+ * nu outside (-1, 1/2). */
+tn_status tn_thin_coating_psd(double kB_T, double f, double r0, double d, double Ys, double nus, double Yc,
+                              double nuc, double phi_c, double *S_out);
+
 /* Measured fused-multiply-add peak of the CUDA cores of `device` in
  * precision TN_F32 or TN_F64 (flop/s, an FMA counted as 2): the roofline
  * denominator of the operator apply, which is bound by arithmetic, not HBM

@@ -1503,6 +1503,19 @@ tn_status tn_layer_energy_parts(tn_ctx *c, const double *u, double *parts_host) 
   return TN_OK;
 }
 
+tn_status tn_thin_coating_psd(double kB_T, double f, double r0, double d, double Ys, double nus, double Yc,
+                              double nuc, double phi_c, double *S_out) {
+  if (!S_out) return fail(TN_EINVAL, "S_out is null");
+  if (!(kB_T > 0.0) || !(f > 0.0) || !(r0 > 0.0) || !(d > 0.0) || !(Ys > 0.0) || !(Yc > 0.0) ||
+      !(nus > -1.0 && nus < 0.5) || !(nuc > -1.0 && nuc < 0.5))
+    return fail(TN_EINVAL, "need kB_T, f, r0, d, Ys, Yc > 0 and -1 < nu < 1/2");
+  const double a = (1.0 + nus) * (1.0 - 2.0 * nus), b = (1.0 + nuc);
+  const double bracket = Yc * Yc * a * a + Ys * Ys * b * b * (1.0 - 2.0 * nuc);
+  *S_out = kB_T / (M_PI * M_PI * f) * (1.0 - nus * nus) / (r0 * Ys) * (d / r0) * phi_c /
+           (Ys * Yc * (1.0 - nuc * nuc) * (1.0 - nus * nus)) * bracket;
+  return TN_OK;
+}
+
 tn_status tn_iso_moduli(double Y, double nu, double *c, double *dc) {
   if (!c) return fail(TN_EINVAL, "c is null");
   if (!(Y > 0.0) || !(nu > -1.0 && nu < 0.5)) return fail(TN_EINVAL, "need Y > 0 and -1 < nu < 1/2");

@@ -32,7 +32,7 @@ SYMBOLS = ["tn_create", "tn_destroy", "tn_last_error", "tn_build_mesh", "tn_ndof
            "tn_solve", "tn_layer_energies", "tn_noise_psd", "tn_precond_apply", "tn_energy_grad", "tn_batch_create", "tn_batch_set",
            "tn_batch_offsets", "tn_batch_energy_grad", "tn_layer_energies_noalloc", "tn_precond_factor_bytes",
            "tn_apply_tuning", "tn_set_apply_variant", "tn_iso_moduli", "tn_fma_peak",
-           "tn_layer_energy_parts"]
+           "tn_layer_energy_parts", "tn_thin_coating_psd"]
 
 
 class MeshDesc(C.Structure):
@@ -102,6 +102,7 @@ def load():
         "tn_noise_psd": (C.c_int, [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, dp]),
         "tn_iso_moduli": (C.c_int, [C.c_double, C.c_double, dp, dp]),
         "tn_fma_peak": (C.c_int, [C.c_int, C.c_int, dp]),
+        "tn_thin_coating_psd": (C.c_int, [C.c_double] * 9 + [dp]),
         "tn_precond_apply": (C.c_int, [vp, C.c_int, C.c_int, vp, vp]),
         "tn_precond_factor_bytes": (C.c_int, [vp, C.c_int, C.POINTER(C.c_longlong)]),
         "tn_energy_grad": (C.c_int, [vp, C.POINTER(SolveOpts), vp, dp, vp, dp, dp, dp,
@@ -408,6 +409,16 @@ def noise_psd(U, phi, kB_T, f, F0):
     _check(load().tn_noise_psd(U.ctypes.data_as(C.POINTER(C.c_double)),
                                phi.ctypes.data_as(C.POINTER(C.c_double)), len(U), kB_T, f, F0,
                                C.byref(out)))
+    return out.value
+
+
+def thin_coating_psd(kB_T, f, r0, d, substrate, coating, phi_c):
+    """Eq. (approx_analytic) through tn_thin_coating_psd; substrate and
+    coating are isotropic material dicts {"Y", "nu"}."""
+    out = C.c_double()
+    _check(load().tn_thin_coating_psd(float(kB_T), float(f), float(r0), float(d), float(substrate["Y"]),
+                                      float(substrate["nu"]), float(coating["Y"]), float(coating["nu"]),
+                                      float(phi_c), C.byref(out)))
     return out.value
 
 

@@ -90,3 +90,20 @@ def test_iso_moduli_host_entry_point(lib):
             assert np.allclose(dc[:, j], ref, rtol=1e-13, atol=0), (j, dc[:, j], ref)
     with pytest.raises(thermonoise.ThermonoiseError):
         thermonoise.iso_moduli(72e9, 0.5)
+
+
+def test_thin_coating_psd_host_entry_point(lib):
+    """Eq. (approx_analytic) in the library against the oracle's first-order
+    thin-coating energy turned into a PSD (the two are pinned to each other
+    for unlike materials in the oracle pins)."""
+    from oracle import observables as ob
+    from paper_2111_06893_gb300 import thermonoise
+    import workloads as W
+    kT, f, r0, d, phi = 300 * ob.BOLTZMANN, 100.0, 1.3, 0.02, 4e-4
+    for sub, coat in [(W.FUSED_SILICA, W.COATING_HIGH), (W.COATING_HIGH, W.FUSED_SILICA)]:
+        S = thermonoise.thin_coating_psd(kT, f, r0, d, sub, coat, phi)
+        U = ob.thin_coating_energy(coat["Y"], coat["nu"], sub["Y"], sub["nu"], d, 1.0, r0)
+        ref = ob.noise_psd(np.array([U]), np.array([phi]), kT, f, 1.0)
+        assert math.isclose(S, ref, rel_tol=1e-13), (S, ref)
+    with pytest.raises(thermonoise.ThermonoiseError):
+        thermonoise.thin_coating_psd(kT, f, r0, -d, W.FUSED_SILICA, W.COATING_HIGH, phi)

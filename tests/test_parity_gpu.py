@@ -425,3 +425,24 @@ def test_energy_parts_of_a_batch_match_single_mirrors():
         sc = thermonoise.setup(d)
         Pi = sc.layer_energy_parts(u[bc.dof_off[i]:bc.dof_off[i + 1]].clone())
         assert np.array_equal(P[lo[i]:lo[i + 1]], Pi), i
+
+
+def test_finite_size_ratio_matches_oracle():
+    """The finite-size study's quantity on a small mirror (R = H = 5 r0,
+    d = 0.04 r0, near-beam square and wedges of 2 and 4 r0): the solved
+    coating noise over the approximate formula, GPU (mixed solve,
+    tn_thin_coating_psd) against the oracle (refined direct solve, its own
+    first-order thin-coating energy), to 1e-9."""
+    from paper_2111_06893_gb300 import thermonoise
+    desc = W.cylinder(5.0, 5.0, [0.04], [W.COATING_HIGH], W.FUSED_SILICA, 1, 3, 3, a=2.0, R1=4.0)
+    op = Operator(Mesh(desc))
+    uo = np.asarray(ob.solve_refined(op.assemble(), op.rhs()), dtype=np.float64)
+    Uo = ob.layer_energies(op, uo)[0]
+    c, s_ = W.COATING_HIGH, W.FUSED_SILICA
+    ratio_o = Uo / ob.thin_coating_energy(c["Y"], c["nu"], s_["Y"], s_["nu"], 0.04, 1.0, 1.0)
+    ctx = thermonoise.setup(desc)
+    u, _ = ctx.solve(mode="mixed", rtol=1e-13, energy_rtol=1e-12, raise_on_error=False)
+    kT, f, phi = 300 * ob.BOLTZMANN, 100.0, 4e-4
+    S = thermonoise.noise_psd(ctx.layer_energies(u)[:1], np.array([phi]), kT, f, 1.0)
+    ratio = S / thermonoise.thin_coating_psd(kT, f, 1.0, 0.04, s_, c, phi)
+    assert abs(ratio - ratio_o) <= 1e-9 * ratio_o, (ratio, ratio_o)
