@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "tn_internal.h"
@@ -824,15 +825,16 @@ static tn_status batch_finalize(tn_ctx *c) {
     s.gline[g] = reinterpret_cast<const int2 *>((size_t)l0);
   }
   std::vector<DevMesh> dms(b->n);
-  std::vector<long long> doff(b->n), foff(b->n);
+  std::vector<long long> doff(b->n + 1), foff(b->n);
   for (int i = 0; i < b->n; ++i) { dms[i] = b->inst[i].dm; doff[i] = b->inst[i].dof_off; foff[i] = b->inst[i].fac_off; }
+  doff[b->n] = b->ndof;  // the last entry closes the last mirror (per-mirror norms)
   cudaError_t e = cudaSuccess;
   auto up = [&](void **dst, const void *src, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(dst, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
   up((void **)&b->d_meshes, dms.data(), sizeof(DevMesh) * b->n);
-  up((void **)&b->d_dof_off, doff.data(), sizeof(long long) * b->n);
+  up((void **)&b->d_dof_off, doff.data(), sizeof(long long) * (b->n + 1));
   up((void **)&b->d_fac_off, foff.data(), sizeof(long long) * b->n);
   up((void **)&b->d_work, work.data(), sizeof(int2) * work.size());
   up((void **)&b->d_lines, lines.data(), sizeof(int2) * lines.size());
@@ -1045,6 +1047,32 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
   if (!is_batch(c)) CU_TRY(tn_launch_diag(c->dm, c->diag64, s), "diag");
   double bb = 0.0;
   CU_TRY(tn::norm2_f64(n, c->b64, c->part_red, c->sum_dev, &bb, s), "norm b");
+  // a batch is converged when every mirror is: the relative residual is the
+  // largest over the mirrors of |r_i| / |b_i| (mirrors with b_i = 0 aside)
+  std::vector<double> bbi, rri;
+  double *seg_dev = nullptr;
+  struct SegFree {
+    double *&p;
+    ~SegFree() { if (p) cudaFree(p); }
+  } seg_free{seg_dev};
+  if (is_batch(c)) {
+    const int nb = c->batch->n;
+    bbi.resize(nb);
+    rri.resize(nb);
+    CU_TRY(cudaMalloc((void **)&seg_dev, sizeof(double) * nb), "per-mirror norms");
+    CU_TRY(tn::segnorm2_f64(nb, c->batch->d_dof_off, c->b64, seg_dev, bbi.data(), s), "norm b per mirror");
+  }
+  // relative residual of r64 (|r|^2 = rr overall)
+  auto rel_res = [&](double rr, cudaError_t *err) {
+    *err = cudaSuccess;
+    if (bbi.empty()) return std::sqrt(rr / bb);
+    *err = tn::segnorm2_f64((int)bbi.size(), c->batch->d_dof_off, c->r64, seg_dev, rri.data(), s);
+    double mx = 0.0;
+    for (size_t i = 0; i < bbi.size(); ++i)
+      if (bbi[i] > 0.0) mx = std::max(mx, std::sqrt(rri[i] / bbi[i]));
+    return std::isfinite(rr) ? mx : rr;
+  };
+  cudaError_t rerr = cudaSuccess;
   const bool zg = o->precond == TN_PC_ZGROUP;
   const bool zl = o->precond == TN_PC_ZLINE || zg;  // a line-type solve (single or grouped lines)
   if (zg) {
@@ -1096,7 +1124,9 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
       double rr = 0.0;
       CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
       r.applies_f64 += 1;
-      if (energy_done || std::sqrt(rr / bb) <= o->rtol || r.inner_iters >= o->max_iter) break;
+      double rel = rel_res(rr, &rerr);
+      CU_TRY(rerr, "norm r per mirror");
+      if (energy_done || rel <= o->rtol || r.inner_iters >= o->max_iter) break;
       x0_zero = false;
     }
     r.status = energy_done ? 1 : 0;
@@ -1126,7 +1156,8 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
     for (int k = 0; k < o->max_outer; ++k) {
       double rr = 0.0;
       CU_TRY(tn::norm2_f64(n, c->r64, c->part_red, c->sum_dev, &rr, s), "norm r");
-      r.rel_residual = std::sqrt(rr / bb);
+      r.rel_residual = rel_res(rr, &rerr);
+      CU_TRY(rerr, "norm r per mirror");
       if (!std::isfinite(rr)) { result = fail(TN_EBREAKDOWN, "non-finite residual"); break; }
       if (r.rel_residual <= o->rtol) {
         // the updated residual drifts from b - A u; confirm on the true one
@@ -1134,7 +1165,8 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
         CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s),
                "residual");
         r.applies_f64 += 1;
-        r.rel_residual = std::sqrt(rr / bb);
+        r.rel_residual = rel_res(rr, &rerr);
+        CU_TRY(rerr, "norm r per mirror");
         if (r.rel_residual <= o->rtol || ++replaced > 3) break;
         best = r.rel_residual;
         stall = 0;
@@ -1194,7 +1226,8 @@ static tn_status solve_impl(tn_ctx *c, const tn_solve_opts *o, const double *rhs
     double rr = 0.0;
     CU_TRY(tn::residual_f64(sys, n, c->b64, u, c->q64, c->r64, c->part_red, c->sum_dev, &rr, s), "residual");
     r.applies_f64 += 1;
-    r.rel_residual = std::sqrt(rr / bb);
+    r.rel_residual = rel_res(rr, &rerr);
+    CU_TRY(rerr, "norm r per mirror");
     if (!(r.rel_residual <= o->rtol) && !energy_ok)
       result = fail(TN_ENOTCONV, "not converged: relative residual %.3e > %.3e after %d iterations",
                     r.rel_residual, o->rtol, r.inner_iters);
@@ -1300,63 +1333,93 @@ static void slab_seed(const tn::HostMesh &hm, const double *slab_z, const int *s
   }
 }
 
-static double host_sum(const double *dev, int n, double *tmp, cudaStream_t st, cudaError_t *err) {
-  *err = cudaMemcpyAsync(tmp, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-  if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += tmp[i];
-  return s;
-}
-
 // dJ/dtheta for every parameter of one mirror, given u, lambda and the layer
 // weights on the device: dual-number operator / energy contractions launched
-// over the slabs a parameter touches; partial sums reduced on the host in a
-// fixed order.  part: device scratch of >= E + 1024 doubles, tmp: host scratch
-// of the same size.
+// over the slabs a parameter touches, every launch into its own slice of
+// `part`, then one copy to the host and fixed-order sums there.
+// seed_dev: n_slabs x (n_slabs N) doubles (the slab seeds of every boundary);
+// matseed: an identity of row stride mat_ld >= 3 n_layers (row 3 L + q
+// seeds modulus q of layer L); part: at least
+// grad_parts(hm) doubles; tmp: host scratch of as many.
+static size_t grad_parts(const tn::HostMesh &hm) {
+  const int S = hm.nslab;
+  size_t n = 256;  // r0
+  for (int b = 1; b <= S; ++b) {
+    const int a0 = b - 2 < 0 ? 0 : b - 2, a1 = b + 2 > S ? S : b + 2;
+    const int k0 = b - 1 < 0 ? 0 : b - 1, k1 = b + 1 > S ? S : b + 1;
+    n += (size_t)(a1 - a0 + k1 - k0) * hm.ncol;
+  }
+  for (int L = 0; L < hm.n_layers; ++L) {
+    int lo = S, hi = -1;
+    for (int q = 0; q < S; ++q)
+      if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
+    if (hi < 0) continue;
+    const int a0 = lo - 1 < 0 ? 0 : lo - 1, a1 = hi + 2 > S ? S : hi + 2;
+    n += 3 * (size_t)(a1 - a0 + hi + 1 - lo) * hm.ncol;
+  }
+  return n;
+}
+
 static cudaError_t grad_contractions(const tn::HostMesh &hm, const DevMesh &dm, const double *slab_z,
                                      const int *slab_log, const double *u, const double *lam, const double *wdev,
                                      double r0, double F0, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
-                                     double *part, double *tmp, double *seed_dev, double *matseed, cudaStream_t s) {
+                                     double *part, double *tmp, double *seed_dev, const double *matseed, int mat_ld,
+                                     cudaStream_t s) {
   const int S = hm.nslab, nl = hm.n_layers, N = hm.N;
-  std::vector<double> seed((size_t)S * N);
-  cudaError_t e = cudaSuccess;
-  dJ_dslab_z[0] = 0.0;
+  std::vector<double> seed((size_t)S * S * N);
+  for (int b = 1; b <= S; ++b) slab_seed(hm, slab_z, slab_log, b, seed.data() + (size_t)(b - 1) * S * N);
+  cudaError_t e = cudaMemcpyAsync(seed_dev, seed.data(), sizeof(double) * seed.size(), cudaMemcpyHostToDevice, s);
+  // launch everything; remember (offset, count) of every sum
+  struct Slice { size_t off; int n; };
+  std::vector<Slice> sl;
+  size_t off = 0;
+  auto slice = [&](int n) { sl.push_back({off, n}); const size_t o = off; off += n; return o; };
   for (int b = 1; b <= S && e == cudaSuccess; ++b) {
-    slab_seed(hm, slab_z, slab_log, b, seed.data());
-    e = cudaMemcpyAsync(seed_dev, seed.data(), sizeof(double) * (size_t)S * N, cudaMemcpyHostToDevice, s);
     DevMesh m = dm;
-    m.d_slabdz = seed_dev;
+    m.d_slabdz = seed_dev + (size_t)(b - 1) * S * N;
     const int a0 = b - 2 < 0 ? 0 : b - 2, a1 = b + 2 > S ? S : b + 2;
     const int k0 = b - 1 < 0 ? 0 : b - 1, k1 = b + 1 > S ? S : b + 1;
-    if (e == cudaSuccess) e = tn_launch_apply_dual(m, a0, a1, u, lam, part, s);
-    const double dAu = e == cudaSuccess ? host_sum(part, (a1 - a0) * hm.ncol, tmp, s, &e) : 0.0;
-    if (e == cudaSuccess) e = tn_launch_energy_dual(m, k0, k1, u, wdev, part, s);
-    const double dK = e == cudaSuccess ? host_sum(part, (k1 - k0) * hm.ncol, tmp, s, &e) : 0.0;
-    dJ_dslab_z[b] = dK - dAu;
+    e = tn_launch_apply_dual(m, a0, a1, u, lam, part + slice((a1 - a0) * hm.ncol), s);
+    if (e == cudaSuccess) e = tn_launch_energy_dual(m, k0, k1, u, wdev, part + slice((k1 - k0) * hm.ncol), s);
   }
   for (int L = 0; L < nl && e == cudaSuccess; ++L) {
     int lo = S, hi = -1;
     for (int q = 0; q < S; ++q)
       if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
+    if (hi < 0) continue;
     for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
-      dJ_dmat[3 * L + q] = 0.0;
-      if (hi < 0) continue;
-      for (int t = 0; t < 3 * nl; ++t) tmp[t] = (t == 3 * L + q) ? 1.0 : 0.0;
-      e = cudaMemcpyAsync(matseed, tmp, sizeof(double) * 3 * nl, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       DevMesh m = dm;
-      m.d_layer_c = matseed;
+      m.d_layer_c = matseed + (size_t)(3 * L + q) * mat_ld;
       const int a0 = lo - 1 < 0 ? 0 : lo - 1, a1 = hi + 2 > S ? S : hi + 2;
-      if (e == cudaSuccess) e = tn_launch_apply_dual(m, a0, a1, u, lam, part, s);
-      const double dAu = e == cudaSuccess ? host_sum(part, (a1 - a0) * hm.ncol, tmp, s, &e) : 0.0;
-      if (e == cudaSuccess) e = tn_launch_energy_dual(m, lo, hi + 1, u, wdev, part, s);
-      const double dK = e == cudaSuccess ? host_sum(part, (hi + 1 - lo) * hm.ncol, tmp, s, &e) : 0.0;
-      dJ_dmat[3 * L + q] = dK - dAu;
+      e = tn_launch_apply_dual(m, a0, a1, u, lam, part + slice((a1 - a0) * hm.ncol), s);
+      if (e == cudaSuccess) e = tn_launch_energy_dual(m, lo, hi + 1, u, wdev, part + slice((hi + 1 - lo) * hm.ncol), s);
     }
   }
-  if (e == cudaSuccess) e = tn_launch_rhs_dr0(dm, r0, F0, lam, part, 256, s);
-  if (e == cudaSuccess) *dJ_dr0 = host_sum(part, 256, tmp, s, &e);
-  return e;
+  if (e == cudaSuccess) e = tn_launch_rhs_dr0(dm, r0, F0, lam, part + slice(256), 256, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, part, sizeof(double) * off, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  auto sum = [&](size_t k) {
+    double acc = 0.0;
+    for (int i = 0; i < sl[k].n; ++i) acc += tmp[sl[k].off + i];
+    return acc;
+  };
+  size_t k = 0;
+  dJ_dslab_z[0] = 0.0;
+  for (int b = 1; b <= S; ++b, k += 2) dJ_dslab_z[b] = sum(k + 1) - sum(k);  // dK - dA u
+  for (int L = 0; L < nl; ++L) {
+    int lo = S, hi = -1;
+    for (int q = 0; q < S; ++q)
+      if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
+    for (int q = 0; q < 3; ++q) {
+      dJ_dmat[3 * L + q] = 0.0;
+      if (hi < 0) continue;
+      dJ_dmat[3 * L + q] = sum(k + 1) - sum(k);
+      k += 2;
+    }
+  }
+  *dJ_dr0 = sum(k);
+  return cudaSuccess;
 }
 
 // the adjoint gradient of the context's mirror or batch (see the header)
@@ -1372,26 +1435,28 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
   if ((st = ensure_ws(c))) return st;
   const int nl = total_layers(c);
   const size_t n = c->ndof;
-  size_t Emax = 0, SNmax = 0;
+  size_t Pmax = 0, SSNmax = 0;
   int NLmax = 0;
-  if (is_batch(c)) {
-    for (int i = 0; i < c->batch->n; ++i) {
-      const tn::HostMesh &hm = c->batch->inst[i].hm;
-      Emax = (size_t)hm.E > Emax ? (size_t)hm.E : Emax;
-      SNmax = (size_t)hm.nslab * hm.N > SNmax ? (size_t)hm.nslab * hm.N : SNmax;
-      NLmax = hm.n_layers > NLmax ? hm.n_layers : NLmax;
-    }
-  } else {
-    Emax = c->hm.E; SNmax = (size_t)c->hm.nslab * c->hm.N; NLmax = c->hm.n_layers;
+  const int ninst = is_batch(c) ? c->batch->n : 1;
+  for (int i = 0; i < ninst; ++i) {
+    const tn::HostMesh &hm = is_batch(c) ? c->batch->inst[i].hm : c->hm;
+    Pmax = std::max(Pmax, grad_parts(hm));
+    SSNmax = std::max(SSNmax, (size_t)hm.nslab * hm.nslab * hm.N);
+    NLmax = std::max(NLmax, hm.n_layers);
   }
   double *wdev = nullptr, *g = nullptr, *lam = lambda, *part = nullptr, *seed_dev = nullptr, *matseed = nullptr;
-  std::vector<double> tmp(Emax + 1024 + 3 * (size_t)NLmax);
+  std::vector<double> tmp(Pmax);
   cudaError_t e = cudaMalloc((void **)&wdev, sizeof(double) * nl);
   if (e == cudaSuccess) e = cudaMalloc((void **)&g, sizeof(double) * n);
   if (e == cudaSuccess && !lam) e = cudaMalloc((void **)&lam, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * (Emax + 1024));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * SNmax);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 3 * NLmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * Pmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * SSNmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 9 * NLmax * NLmax);
+  if (e == cudaSuccess) {  // the moduli seeds: identity of 3 NLmax (row 3L + q seeds modulus q of layer L)
+    std::vector<double> eye((size_t)9 * NLmax * NLmax, 0.0);
+    for (int t = 0; t < 3 * NLmax; ++t) eye[(size_t)t * 3 * NLmax + t] = 1.0;
+    e = cudaMemcpy(matseed, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice);
+  }
   tn_solve_report r{};
   cudaStream_t s = c->stream;
   auto cleanup = [&]() {
@@ -1421,14 +1486,14 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
   tn_status result = st;
   if (!is_batch(c)) {
     e = grad_contractions(c->hm, c->dm, c->slab_z_host, c->slab_log_host, u, lam, wdev, c->r0, c->F0, dJ_dslab_z,
-                          dJ_dr0, dJ_dmat, part, tmp.data(), seed_dev, matseed, s);
+                          dJ_dr0, dJ_dmat, part, tmp.data(), seed_dev, matseed, 3 * NLmax, s);
   } else {
     size_t zoff = 0;
     for (int i = 0; i < c->batch->n && e == cudaSuccess; ++i) {
       const BatchInst &q = c->batch->inst[i];
       e = grad_contractions(q.hm, q.dm, q.slab_z.data(), q.slab_log.data(), u + q.dof_off, lam + q.dof_off,
                             wdev + q.layer_off, q.r0, q.F0, dJ_dslab_z + zoff, dJ_dr0 + i,
-                            dJ_dmat + 3 * (size_t)q.layer_off, part, tmp.data(), seed_dev, matseed, s);
+                            dJ_dmat + 3 * (size_t)q.layer_off, part, tmp.data(), seed_dev, matseed, 3 * NLmax, s);
       zoff += q.hm.nslab + 1;
     }
   }

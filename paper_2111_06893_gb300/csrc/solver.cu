@@ -245,6 +245,17 @@ __global__ void k_fill(size_t n, T *__restrict__ v, T val) {
 }
 
 
+// out[i] = sum of squares of v over segment i = [off[i], off[i + 1]) (one
+// block per segment, fixed order; off has nseg + 1 entries, off[nseg] = n)
+__global__ void k_segsumsq(const long long *__restrict__ off, const double *__restrict__ v,
+                           double *__restrict__ out) {
+  const long long a = off[blockIdx.x], b = off[blockIdx.x + 1];
+  double acc = 0.0, dummy = 0.0;
+  for (long long t = a + threadIdx.x; t < b; t += blockDim.x) acc += v[t] * v[t];
+  block_sum2(acc, dummy);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
 // ---- flexible CG (FP64 outer of the mixed-precision solve)
 // dots[j] partials: a . B_j for up to 16 vectors B_j, fixed partition
 __global__ void k_multidot(size_t n, const double *__restrict__ a, const double *const *__restrict__ B, int nb,
@@ -586,6 +597,15 @@ cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_d
   TN_CU(cudaStreamSynchronize(st));
   *out_host = tmp[0];
   return cudaSuccess;
+}
+
+cudaError_t segnorm2_f64(int nseg, const long long *off, const double *v, double *out_dev, double *out_host,
+                         cudaStream_t st) {
+  g_launches += 1;
+  k_segsumsq<<<nseg, 256, 0, st>>>(off, v, out_dev);
+  TN_CU(cudaGetLastError());
+  TN_CU(cudaMemcpyAsync(out_host, out_dev, sizeof(double) * nseg, cudaMemcpyDeviceToHost, st));
+  return cudaStreamSynchronize(st);
 }
 
 cudaError_t cast_scaled(size_t n, const double *r64, double scale, float *r32, float *d32, cudaStream_t st) {

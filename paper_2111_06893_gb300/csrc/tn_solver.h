@@ -71,6 +71,9 @@ cudaError_t residual_f64(const OpSys &sys, size_t n, const double *b, const doub
                          double *part_red, double *sum_dev, double *rr_host, cudaStream_t st);
 cudaError_t norm2_f64(size_t n, const double *v, double *part_red, double *sum_dev, double *out_host,
                       cudaStream_t st);
+// per-segment squared norms: out[i] = |v[off[i] .. off[i + 1])|^2 (device and host copies; synchronises)
+cudaError_t segnorm2_f64(int nseg, const long long *off, const double *v, double *out_dev, double *out_host,
+                         cudaStream_t st);
 cudaError_t cast_scaled(size_t n, const double *r64, double scale, float *r32, float *d32, cudaStream_t st);
 cudaError_t refine_update(size_t n, double *x, const float *d, double scale, cudaStream_t st);
 cudaError_t fill_f64(size_t n, double *v, double val, cudaStream_t st);
