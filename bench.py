@@ -56,19 +56,18 @@ def fp32_apply_flops_per_dof(N):
     return per_elem / (3 * N ** 3)
 
 
-# DRAM bytes (read + write) of one preconditioner solve (no residual update),
-# summed over its launches, from `ncu --set full -k regex:zgroup_solve_kernel`
-# of `bench.py --mode apply --workload single_coating`; absent where no
-# capture of the current kernels exists
-ZLINE_TRAFFIC = {("single_coating", "zgroup_solve_kernel<7,G,float,0>, one launch per (N, G) class on concurrent streams"):
-                 (43236096 + 512 + 2476544 + 0 + 131932160 + 996608 + 102644224 + 581376) * 1.0}
+# DRAM bytes (read + write) of one preconditioner solve (no residual update)
+# from `ncu --set full -k regex:zgroup_packed_kernel` of `bench.py --mode
+# apply --workload single_coating`; absent where no capture of the current
+# kernel exists
+ZLINE_TRAFFIC = {("single_coating", "zgroup_packed_kernel<7,float,0>"): 322276608.0 + 9202176.0}
 
 
 # DRAM bytes (read + write) of one FP32 apply per occupancy variant, from
 # `ncu --set full -k regex:apply2_kernel` of `bench.py --mode apply --workload
-# single_coating` (variant 1: its register spills add local-memory traffic)
-APPLY_TRAFFIC = {("single_coating", "apply2_kernel<7,float,0>"): 8144128.0,
-                 ("single_coating", "apply2_kernel<7,float,1>"): 10237184.0 + 704768.0}
+# single_coating` (variant 0 captured; variant 1's register spills add
+# local-memory traffic, not captured for the current kernel)
+APPLY_TRAFFIC = {("single_coating", "apply2_kernel<7,float,0>"): 8148736.0}
 
 
 def measured_peaks():
@@ -658,8 +657,8 @@ def main():
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
     if pc == "zgroup":
-        zkernel = (f"zgroup_solve_kernel<{'N' if batched else N},G,float,0>, "
-                   "one launch per (N, G) class on concurrent streams")
+        zkernel = (f"zgroup_packed_kernel<{'N' if batched else N},float,0>"
+                   + (", one launch per degree" if batched else ""))
     else:
         zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
                    else f"zline_solve_kernel<{N},float,float,0>")

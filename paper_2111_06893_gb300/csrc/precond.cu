@@ -1377,6 +1377,9 @@ cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const 
   if (err != cudaSuccess) return err;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!per_sm[dev]) {
+    // shared memory before L1: the CTAs per SM are limited by the staging rings
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return err;
     int b = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kZgThreads, sm);
     if (err != cudaSuccess) return err;
