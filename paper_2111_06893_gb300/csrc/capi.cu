@@ -1334,13 +1334,14 @@ static void slab_seed(const tn::HostMesh &hm, const double *slab_z, const int *s
 }
 
 // dJ/dtheta for every parameter of one mirror, given u, lambda and the layer
-// weights on the device: dual-number operator / energy contractions launched
-// over the slabs a parameter touches, every launch into its own slice of
-// `part`, then one copy to the host and fixed-order sums there.
+// weights on the device: the dual-number operator contractions of every
+// parameter (over the slabs it touches) in one launch and the energy
+// contractions in another (work lists of (parameter, element) pairs), one
+// partial per CTA, then one copy to the host and fixed-order sums there.
 // seed_dev: n_slabs x (n_slabs N) doubles (the slab seeds of every boundary);
 // matseed: an identity of row stride mat_ld >= 3 n_layers (row 3 L + q
-// seeds modulus q of layer L); part: at least
-// grad_parts(hm) doubles; tmp: host scratch of as many.
+// seeds modulus q of layer L); part and work_dev: grad_parts(hm) entries;
+// pseed_dev: 2 per parameter; tmp: host scratch of grad_parts(hm) doubles.
 static size_t grad_parts(const tn::HostMesh &hm) {
   const int S = hm.nslab;
   size_t n = 256;  // r0
@@ -1364,61 +1365,69 @@ static cudaError_t grad_contractions(const tn::HostMesh &hm, const DevMesh &dm, 
                                      const int *slab_log, const double *u, const double *lam, const double *wdev,
                                      double r0, double F0, double *dJ_dslab_z, double *dJ_dr0, double *dJ_dmat,
                                      double *part, double *tmp, double *seed_dev, const double *matseed, int mat_ld,
-                                     cudaStream_t s) {
-  const int S = hm.nslab, nl = hm.n_layers, N = hm.N;
+                                     int2 *work_dev, const double **pseed_dev, cudaStream_t s) {
+  const int S = hm.nslab, nl = hm.n_layers, N = hm.N, nc = hm.ncol;
   std::vector<double> seed((size_t)S * S * N);
   for (int b = 1; b <= S; ++b) slab_seed(hm, slab_z, slab_log, b, seed.data() + (size_t)(b - 1) * S * N);
-  cudaError_t e = cudaMemcpyAsync(seed_dev, seed.data(), sizeof(double) * seed.size(), cudaMemcpyHostToDevice, s);
-  // launch everything; remember (offset, count) of every sum
-  struct Slice { size_t off; int n; };
-  std::vector<Slice> sl;
-  size_t off = 0;
-  auto slice = [&](int n) { sl.push_back({off, n}); const size_t o = off; off += n; return o; };
-  for (int b = 1; b <= S && e == cudaSuccess; ++b) {
-    DevMesh m = dm;
-    m.d_slabdz = seed_dev + (size_t)(b - 1) * S * N;
-    const int a0 = b - 2 < 0 ? 0 : b - 2, a1 = b + 2 > S ? S : b + 2;
-    const int k0 = b - 1 < 0 ? 0 : b - 1, k1 = b + 1 > S ? S : b + 1;
-    e = tn_launch_apply_dual(m, a0, a1, u, lam, part + slice((a1 - a0) * hm.ncol), s);
-    if (e == cudaSuccess) e = tn_launch_energy_dual(m, k0, k1, u, wdev, part + slice((k1 - k0) * hm.ncol), s);
-  }
-  for (int L = 0; L < nl && e == cudaSuccess; ++L) {
-    int lo = S, hi = -1;
-    for (int q = 0; q < S; ++q)
-      if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
-    if (hi < 0) continue;
-    for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
-      DevMesh m = dm;
-      m.d_layer_c = matseed + (size_t)(3 * L + q) * mat_ld;
-      const int a0 = lo - 1 < 0 ? 0 : lo - 1, a1 = hi + 2 > S ? S : hi + 2;
-      e = tn_launch_apply_dual(m, a0, a1, u, lam, part + slice((a1 - a0) * hm.ncol), s);
-      if (e == cudaSuccess) e = tn_launch_energy_dual(m, lo, hi + 1, u, wdev, part + slice((hi + 1 - lo) * hm.ncol), s);
-    }
-  }
-  if (e == cudaSuccess) e = tn_launch_rhs_dr0(dm, r0, F0, lam, part + slice(256), 256, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, part, sizeof(double) * off, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  auto sum = [&](size_t k) {
-    double acc = 0.0;
-    for (int i = 0; i < sl[k].n; ++i) acc += tmp[sl[k].off + i];
-    return acc;
-  };
-  size_t k = 0;
-  dJ_dslab_z[0] = 0.0;
-  for (int b = 1; b <= S; ++b, k += 2) dJ_dslab_z[b] = sum(k + 1) - sum(k);  // dK - dA u
+  // parameters: slab boundaries b = 1..S, then (layer L, modulus q) of the
+  // layers that own slabs; per parameter the slabs of its operator and
+  // energy contractions
+  struct Param { int a0, a1, k0, k1; const double *ss, *ms; };
+  std::vector<Param> prm;
+  for (int b = 1; b <= S; ++b)
+    prm.push_back({b - 2 < 0 ? 0 : b - 2, b + 2 > S ? S : b + 2, b - 1 < 0 ? 0 : b - 1, b + 1 > S ? S : b + 1,
+                   seed_dev + (size_t)(b - 1) * S * N, nullptr});
+  std::vector<int> mat_param(3 * nl, -1);
   for (int L = 0; L < nl; ++L) {
     int lo = S, hi = -1;
     for (int q = 0; q < S; ++q)
       if (hm.slab_layer[q] == L) { lo = q < lo ? q : lo; hi = q > hi ? q : hi; }
+    if (hi < 0) continue;
     for (int q = 0; q < 3; ++q) {
-      dJ_dmat[3 * L + q] = 0.0;
-      if (hi < 0) continue;
-      dJ_dmat[3 * L + q] = sum(k + 1) - sum(k);
-      k += 2;
+      mat_param[3 * L + q] = (int)prm.size();
+      prm.push_back({lo - 1 < 0 ? 0 : lo - 1, hi + 2 > S ? S : hi + 2, lo, hi + 1, nullptr,
+                     matseed + (size_t)(3 * L + q) * mat_ld});
     }
   }
-  *dJ_dr0 = sum(k);
+  // work lists (parameter, element), the operator's first, then the energy's
+  std::vector<int2> work;
+  std::vector<size_t> aoff(prm.size() + 1), eoff(prm.size() + 1);
+  std::vector<const double *> ps(2 * prm.size());
+  for (size_t p = 0; p < prm.size(); ++p) {
+    aoff[p] = work.size();
+    for (int e = prm[p].a0 * nc; e < prm[p].a1 * nc; ++e) work.push_back(make_int2((int)p, e));
+    ps[2 * p] = prm[p].ss;
+    ps[2 * p + 1] = prm[p].ms;
+  }
+  aoff[prm.size()] = work.size();
+  const size_t na = work.size();
+  for (size_t p = 0; p < prm.size(); ++p) {
+    eoff[p] = work.size() - na;
+    for (int e = prm[p].k0 * nc; e < prm[p].k1 * nc; ++e) work.push_back(make_int2((int)p, e));
+  }
+  eoff[prm.size()] = work.size() - na;
+  const size_t ne = work.size() - na;
+  cudaError_t e = cudaMemcpyAsync(seed_dev, seed.data(), sizeof(double) * seed.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(work_dev, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pseed_dev, ps.data(), sizeof(double *) * ps.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = tn_launch_apply_dual_work(dm, work_dev, (int)na, pseed_dev, u, lam, part, s);
+  if (e == cudaSuccess) e = tn_launch_energy_dual_work(dm, work_dev + na, (int)ne, pseed_dev, u, wdev, part + na, s);
+  if (e == cudaSuccess) e = tn_launch_rhs_dr0(dm, r0, F0, lam, part + na + ne, 256, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, part, sizeof(double) * (na + ne + 256), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // also keeps the host arrays alive until copied
+  if (e != cudaSuccess) return e;
+  auto sum = [&](size_t a, size_t b) {
+    double acc = 0.0;
+    for (size_t i = a; i < b; ++i) acc += tmp[i];
+    return acc;
+  };
+  auto dJ = [&](size_t p) {  // dK - dA u
+    return sum(na + eoff[p], na + eoff[p + 1]) - sum(aoff[p], aoff[p + 1]);
+  };
+  dJ_dslab_z[0] = 0.0;
+  for (int b = 1; b <= S; ++b) dJ_dslab_z[b] = dJ(b - 1);
+  for (int t = 0; t < 3 * nl; ++t) dJ_dmat[t] = mat_param[t] >= 0 ? dJ(mat_param[t]) : 0.0;
+  *dJ_dr0 = sum(na + ne, na + ne + 256);
   return cudaSuccess;
 }
 
@@ -1445,6 +1454,8 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
     NLmax = std::max(NLmax, hm.n_layers);
   }
   double *wdev = nullptr, *g = nullptr, *lam = lambda, *part = nullptr, *seed_dev = nullptr, *matseed = nullptr;
+  int2 *work_dev = nullptr;
+  const double **pseed_dev = nullptr;
   std::vector<double> tmp(Pmax);
   cudaError_t e = cudaMalloc((void **)&wdev, sizeof(double) * nl);
   if (e == cudaSuccess) e = cudaMalloc((void **)&g, sizeof(double) * n);
@@ -1452,6 +1463,8 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
   if (e == cudaSuccess) e = cudaMalloc((void **)&part, sizeof(double) * Pmax);
   if (e == cudaSuccess) e = cudaMalloc((void **)&seed_dev, sizeof(double) * SSNmax);
   if (e == cudaSuccess) e = cudaMalloc((void **)&matseed, sizeof(double) * 9 * NLmax * NLmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&work_dev, sizeof(int2) * Pmax);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&pseed_dev, sizeof(double *) * 2 * (SSNmax + 3 * (size_t)NLmax));
   if (e == cudaSuccess) {  // the moduli seeds: identity of 3 NLmax (row 3L + q seeds modulus q of layer L)
     std::vector<double> eye((size_t)9 * NLmax * NLmax, 0.0);
     for (int t = 0; t < 3 * NLmax; ++t) eye[(size_t)t * 3 * NLmax + t] = 1.0;
@@ -1466,6 +1479,8 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
     if (part) cudaFree(part);
     if (seed_dev) cudaFree(seed_dev);
     if (matseed) cudaFree(matseed);
+    if (work_dev) cudaFree(work_dev);
+    if (pseed_dev) cudaFree(pseed_dev);
   };
   if (e != cudaSuccess) { cleanup(); cudaGetLastError(); return fail(TN_ENOMEM, "gradient workspace"); }
   // adjoint source g = sum_i w_i K_i u per mirror
@@ -1486,14 +1501,15 @@ static tn_status grad_impl(tn_ctx *c, const tn_solve_opts *o, const double *u, c
   tn_status result = st;
   if (!is_batch(c)) {
     e = grad_contractions(c->hm, c->dm, c->slab_z_host, c->slab_log_host, u, lam, wdev, c->r0, c->F0, dJ_dslab_z,
-                          dJ_dr0, dJ_dmat, part, tmp.data(), seed_dev, matseed, 3 * NLmax, s);
+                          dJ_dr0, dJ_dmat, part, tmp.data(), seed_dev, matseed, 3 * NLmax, work_dev, pseed_dev, s);
   } else {
     size_t zoff = 0;
     for (int i = 0; i < c->batch->n && e == cudaSuccess; ++i) {
       const BatchInst &q = c->batch->inst[i];
       e = grad_contractions(q.hm, q.dm, q.slab_z.data(), q.slab_log.data(), u + q.dof_off, lam + q.dof_off,
                             wdev + q.layer_off, q.r0, q.F0, dJ_dslab_z + zoff, dJ_dr0 + i,
-                            dJ_dmat + 3 * (size_t)q.layer_off, part, tmp.data(), seed_dev, matseed, 3 * NLmax, s);
+                            dJ_dmat + 3 * (size_t)q.layer_off, part, tmp.data(), seed_dev, matseed, 3 * NLmax,
+                            work_dev, pseed_dev, s);
       zoff += q.hm.nslab + 1;
     }
   }

@@ -250,10 +250,23 @@ constexpr size_t apply_smem() {
 
 // T = double / float: y = A u (and optionally partial[e] = u_e . y_e).
 // T = Dual: derivative of A u along the seeded direction; partial[e] = lam_e . (dA u)_e, y unused.
+// work (optional, derivatives): CTA b contracts element work[b].y along
+// parameter work[b].x, whose seeds are pseed[2 work[b].x] (d(dz/dzeta) per
+// slab node) and pseed[2 work[b].x + 1] (d(c11, c12, c44) per layer),
+// either may be nullptr; partial[b] as before.
 template <int N, typename T, typename TIO>
 __global__ void __launch_bounds__(nthreads<N>())
-apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict__ y, double *__restrict__ partial,
-             const double *__restrict__ lam) {
+apply_kernel(const DevMesh m0, int e0, const TIO *__restrict__ u, TIO *__restrict__ y, double *__restrict__ partial,
+             const double *__restrict__ lam, const int2 *__restrict__ work = nullptr,
+             const double *const *__restrict__ pseed = nullptr) {
+  DevMesh m = m0;
+  int ework = -1;
+  if (work) {
+    const int2 wk = work[blockIdx.x];
+    ework = wk.y;
+    m.d_slabdz = pseed[2 * wk.x];
+    m.d_layer_c = pseed[2 * wk.x + 1];
+  }
   constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *su = reinterpret_cast<T *>(smem_raw);  // [3][n]
@@ -265,7 +278,7 @@ apply_kernel(const DevMesh m, int e0, const TIO *__restrict__ u, TIO *__restrict
   __shared__ T nbc[6][3];
   __shared__ double red[NT / 32];
 
-  const int e = e0 + blockIdx.x, tid = threadIdx.x;
+  const int e = work ? ework : e0 + blockIdx.x, tid = threadIdx.x;
   const int s = e / m.ncol, c = e - s * m.ncol;
   const TIO *ue = u + (size_t)e * 3 * n;
   for (int t = tid; t < 3 * n; t += NT) su[t] = T(ue[t]);
@@ -1203,12 +1216,21 @@ __global__ void diag_kernel(const DevMesh m, double *__restrict__ dg) {
 // along the seeded direction instead; scaled by w[layer] if w is given.
 template <int N, typename T>
 __global__ void __launch_bounds__(nthreads<N>())
-energy_kernel(const DevMesh m, int e0, const double *__restrict__ u, const double *__restrict__ w,
-              double *__restrict__ elem) {
+energy_kernel(const DevMesh m0, int e0, const double *__restrict__ u, const double *__restrict__ w,
+              double *__restrict__ elem, const int2 *__restrict__ work = nullptr,
+              const double *const *__restrict__ pseed = nullptr) {
+  DevMesh m = m0;  // work: as for apply_kernel
+  int ework = -1;
+  if (work) {
+    const int2 wk = work[blockIdx.x];
+    ework = wk.y;
+    m.d_slabdz = pseed[2 * wk.x];
+    m.d_layer_c = pseed[2 * wk.x + 1];
+  }
   constexpr int n = N * N * N, N2 = N * N, NT = nthreads<N>();
   __shared__ double su[3 * n];
   __shared__ double red[NT / 32];
-  const int e = e0 + blockIdx.x, tid = threadIdx.x;
+  const int e = work ? ework : e0 + blockIdx.x, tid = threadIdx.x;
   const int s = e / m.ncol, c = e - s * m.ncol;
   for (int t = tid; t < 3 * n; t += NT) su[t] = u[(size_t)e * 3 * n + t];
   __syncthreads();
@@ -1602,6 +1624,34 @@ cudaError_t tn_launch_apply_dual(const DevMesh &m, int s0, int s1, const double 
 cudaError_t tn_launch_energy_dual(const DevMesh &m, int s0, int s1, const double *u, const double *w,
                                   double *epart, cudaStream_t st) {
   TN_DISPATCH_N(return launch_energy_dual_n<NN>(m, s0, s1, u, w, epart, st))
+}
+
+cudaError_t tn_launch_apply_dual_work(const DevMesh &m, const int2 *work, int nwork, const double *const *pseed,
+                                      const double *u, const double *lam, double *part, cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  TN_DISPATCH_N({
+    constexpr size_t sm = apply_smem<NN, Dual>();
+    static int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+      cudaError_t err = cudaFuncSetAttribute(apply_kernel<NN, Dual, double>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (err != cudaSuccess) return err;
+      configured_device = dev;
+    }
+    apply_kernel<NN, Dual, double><<<nwork, nthreads<NN>(), sm, st>>>(m, 0, u, nullptr, part, lam, work, pseed);
+    return cudaGetLastError();
+  })
+}
+
+cudaError_t tn_launch_energy_dual_work(const DevMesh &m, const int2 *work, int nwork, const double *const *pseed,
+                                       const double *u, const double *w, double *epart, cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  TN_DISPATCH_N({
+    energy_kernel<NN, Dual><<<nwork, nthreads<NN>(), 0, st>>>(m, 0, u, w, epart, work, pseed);
+    return cudaGetLastError();
+  })
 }
 
 cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const double *w, double *g,

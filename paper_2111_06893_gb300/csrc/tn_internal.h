@@ -163,6 +163,13 @@ cudaError_t tn_launch_apply_dual(const DevMesh &m, int s0, int s1, const double 
                                  double *part, cudaStream_t st);
 cudaError_t tn_launch_energy_dual(const DevMesh &m, int s0, int s1, const double *u, const double *w,
                                   double *epart, cudaStream_t st);
+// the same for many parameters in one launch each: CTA b contracts element
+// work[b].y along parameter work[b].x, seeded by pseed[2 p] (d_slabdz) and
+// pseed[2 p + 1] (d_layer_c), device arrays; part[b] / epart[b]
+cudaError_t tn_launch_apply_dual_work(const DevMesh &m, const int2 *work, int nwork, const double *const *pseed,
+                                      const double *u, const double *lam, double *part, cudaStream_t st);
+cudaError_t tn_launch_energy_dual_work(const DevMesh &m, const int2 *work, int nwork, const double *const *pseed,
+                                       const double *u, const double *w, double *epart, cudaStream_t st);
 // g = sum_i w_i K_i u (the derivative of sum_i w_i U_i with respect to u)
 cudaError_t tn_launch_energy_source(const DevMesh &m, const double *u, const double *w, double *g,
                                     cudaStream_t st);
