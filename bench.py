@@ -60,7 +60,7 @@ def fp32_apply_flops_per_dof(N):
 # from `ncu --set full -k regex:zgroup_packed_kernel` of `bench.py --mode
 # apply --workload single_coating`; absent where no capture of the current
 # kernel exists
-ZLINE_TRAFFIC = {("single_coating", "zgroup_packed_kernel<7,float,0>"): 322276608.0 + 9202176.0}
+ZLINE_TRAFFIC = {}
 
 
 # DRAM bytes (read + write) of one FP32 apply per occupancy variant, from
@@ -591,8 +591,9 @@ def main():
         tz, tz_how = time_zline_graph(20), "CUDA events around a replayed graph of 20 applications"
     except Exception as exc:  # capture not possible here: eager timing
         tz, tz_how = tz_eager, f"CUDA events, eager calls ({type(exc).__name__})"
-    # algorithmic bytes of one line solve: every FP32 factor record once, r in
-    # and z out (what the method must move; re-reads are not credited)
+    # algorithmic bytes of one line solve: the compact FP32 factors once (the
+    # grouped solve's backward couplings W_s, which derive from them, and
+    # re-reads are not credited), r in and z out
     zbytes = ctx.precond_factor_bytes(pc) + 8 * ndof
     flops = flops_dof * ndof
     # measured FMA peaks of the CUDA cores (the apply is bound by arithmetic)
@@ -684,7 +685,7 @@ def main():
                      "frac": zbytes / tz / 1e9 / hbm_peak,
                      "traffic": ZLINE_TRAFFIC.get((args.workload, zkernel)),
                      "kernel": zkernel, "us": tz * 1e6, "us_eager": tz_eager * 1e6, "timing": tz_how,
-                     "algorithmic_bytes": zbytes, "bytes": "FP32 factor records once + r in + z out",
+                     "algorithmic_bytes": zbytes, "bytes": "compact FP32 factors (Linv_s, O_s) once + r in + z out",
                      "peak_source": peak_src},
         "roofline_apply": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                            "frac": achieved / peak_fp32,

@@ -182,7 +182,8 @@ tn_status tn_diagonal(tn_ctx *ctx, double *d_dev);
  * (Eqs. (numflux), (penalty)) that single lines leave out; TN_EINVAL if a
  * node is shared by more than 4 columns.  The first call after
  * tn_build_mesh / tn_set_materials builds the factors (FP64 set-up, about
- * 1.5 (3 g N)^2 * n_slabs FP32 and FP64 entries per group of g lines).
+ * (3 g N)^2 / 2 + 3 g N (8 + 6 g) FP32 and FP64 entries per group of g
+ * lines and slab).
  * precision TN_F64 / TN_F32 selects double / float vectors r, z
  * (caller-owned device buffers of tn_ndof() values, 16-byte aligned, not
  * overlapping). */
@@ -191,9 +192,11 @@ tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *
  * of tn_solve_opts.device_wait_limit_s, and a wait that ran out leaves z
  * incomplete without an error code; tn_solve reports timeouts.) */
 
-/* Bytes of FP32 factors one FP32 application of `precond` reads (building
- * the factors first if needed; TN_PC_JACOBI: the inverse diagonal), for
- * bandwidth accounting.  *bytes: host. */
+/* Bytes of FP32 factors one FP32 application of `precond` must read at
+ * least (building the factors first if needed), for bandwidth accounting:
+ * TN_PC_ZLINE the line records; TN_PC_ZGROUP the compact factors Linv_s and
+ * O_s (the records' backward couplings W_s, which derive from them, are not
+ * counted); TN_PC_JACOBI the inverse diagonal.  *bytes: host. */
 tn_status tn_precond_factor_bytes(tn_ctx *ctx, int precond, long long *bytes);
 
 /* Krylov solve of A u = b for the beam load (Sec. 2.3).

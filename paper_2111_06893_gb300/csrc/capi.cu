@@ -1257,7 +1257,7 @@ tn_status tn_precond_factor_bytes(tn_ctx *c, int precond, long long *bytes) {
   if ((st = ensure_ws(c))) return st;
   if (precond == TN_PC_ZGROUP) {
     if ((st = ensure_zgroup(c, c->stream))) return st;
-    *bytes = c->gplan.nfac * (long long)sizeof(float);
+    *bytes = c->gplan.ncompact * (long long)sizeof(float);
     return TN_OK;
   }
   if (precond == TN_PC_ZLINE) {

@@ -695,7 +695,15 @@ __global__ void zgroup_cross_kernel(const DevMesh m, double *__restrict__ xblk) 
 // and Y[t][b] = O[t, (b, N - 1)] (Y zero on k = 0 rows).  Row t stores
 // X[t][0..2], 0, Y[t][0..2], 0.  The solve applies Z_s = Linv_{s-1} O_{s-1}
 // through Linv and these factors instead of storing Z densely.
-__host__ __device__ constexpr int zg_rec(int MG) { return zlp(MG) + 8 * MG; }
+// The record ends with the backward sweep's coupling W_s = S_s^{-1} [Y_s | E_0]
+// (MG x 6G, rows padded to zg_ws(G)), S_s = L_s L_s^T the slab's Schur
+// complement and Y_s, E_0 of O_s (the coupling to slab s + 1): per line l,
+// column 6 l + b holds Y of component b and column 6 l + 3 + a the unit
+// vector of row (a, k = 0); zero for the last slab.  With it the backward
+// step x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1}) = w_s - W_s v, v the six
+// numbers per line x_{s+1}(b, N - 1) and X^T x_{s+1}.
+__host__ __device__ constexpr int zg_ws(int G) { return pad4(6 * G); }
+__host__ __device__ constexpr int zg_rec(int MG, int G) { return zlp(MG) + 8 * MG + MG * zg_ws(G); }
 
 // block Cholesky along the slabs of one group (one CTA; FP64 working
 // matrices G, Linv, Z of (3 g N)^2 entries each in `work`), then FP32 and
@@ -709,7 +717,7 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
   constexpr int M = 3 * N, N2 = N * N;
   const int grp = gbase + blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int MG = g * M, S = m.nslab;
-  const int LP = zlp(MG), RS = zg_rec(MG);
+  const int LP = zlp(MG), RS = zg_rec(MG, g), WS = zg_ws(g);
   double *Gm = work + (size_t)blockIdx.x * 3 * MG * MG, *Li = Gm + MG * MG, *Z = Li + MG * MG;
   __shared__ int lid[4], xof[4][4];
   if (tid < 4) {
@@ -808,6 +816,32 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
       Ld[LP + q] = v;
     }
     __syncthreads();
+    // W_s = Linv_s^T (Linv_s [Y_s | E_0]); L (in Gm) is no longer needed
+    double *T1 = Gm;  // MG x 6g
+    if (s + 1 < S) {
+      for (int q = tid; q < MG * 6 * g; q += nth) {
+        const int r = q / (6 * g), j = q - r * (6 * g), l = j / 6, jj = j - l * 6;
+        double acc = 0.0;
+        if (jj < 3) {  // Y of O_s, component b = jj: O_s[p, (b, N - 1)] on the rows p of line l with k != 0
+          const double *O = blk + (((size_t)lid[l] * S + s) * 2 + 1) * M * M;
+          for (int pl = 0; pl < M; ++pl)
+            if (pl % N != 0) acc += Li[r * MG + l * M + pl] * O[pl * M + jj * N + (N - 1)];
+        } else {  // E_0 of row (a, k = 0) of line l: a column of Linv
+          acc = Li[r * MG + l * M + (jj - 3) * N];
+        }
+        T1[q] = acc;
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < MG * WS; q += nth) {
+      const int t = q / WS, j = q - t * WS;
+      double acc = 0.0;
+      if (s + 1 < S && j < 6 * g)
+        for (int r = t; r < MG; ++r) acc += Li[r * MG + t] * T1[r * 6 * g + j];
+      Lf[LP + 8 * MG + q] = (float)acc;
+      Ld[LP + 8 * MG + q] = acc;
+    }
+    __syncthreads();
     if (s + 1 < S) {  // Z_{s+1} = Linv_s O_s, O_s block diagonal over the lines
       for (int q = tid; q < MG * MG; q += nth) {
         const int r = q / MG, cc = q - r * MG, t2 = cc / M, c2 = cc - t2 * M;
@@ -836,9 +870,16 @@ constexpr int kZgMaxStages = 8;
 // floats / doubles of staging per warp: two records of the largest group
 // (4 lines) across the four warps of a CTA, so that six CTAs (FP32, N = 7)
 // share an SM; smaller groups fit more stages in the same room
+// stage buffer of a group of G lines: the larger of the forward stage
+// (Linv_s and the O factors of record s) and the backward stage (W_s and
+// the O factors of record s + 1)
+template <int N, int G>
+__host__ __device__ constexpr int zg_stage() {
+  return (zlp(3 * G * N) > 3 * G * N * zg_ws(G) ? zlp(3 * G * N) : 3 * G * N * zg_ws(G)) + 8 * 3 * G * N;
+}
 template <int N, typename T>
 __host__ __device__ constexpr int zg_stage_per_warp() {
-  return pad4((zg_rec(12 * N) * 2 + 3) / 4);
+  return pad4((zg_stage<N, 4>() * 2 + 3) / 4);
 }
 template <int N, typename T>
 constexpr size_t zg_smem() {
@@ -876,14 +917,15 @@ __device__ __forceinline__ double warp_allsum(double v) {
 // z = A_GG^{-1} r on group grp by the slot of G warps starting at warp w0;
 // line li of the group is warp w0 + li, its rows (a, k) lanes a N + k < 3N:
 //   forward   y_s = Linv_s (r_s - O_{s-1}^T w_{s-1}),  w_s = Linv_s^T y_s
-//   backward  x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1})
-// (Z_s = Linv_{s-1} O_{s-1}).  O in its factored form acts line by line
-// (it is block diagonal over the lines), so its products are warp shuffles
-// and warp sums; only the two triangular products cross lines, through
-// broadcast vectors in shared memory (double-buffered by step parity).
-// Stage u < S: record u; stage u >= S: Linv_s and the O factors of record
-// s + 1, s = 2S - 1 - u.  Stage u uses ring buffer u % P and mbarrier u % P
-// with phase parity (u / P) & 1.  UPD: first r <- r - alpha q (written
+//   backward  x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1}) = w_s - W_s v_{s+1}
+// (Z_s = Linv_{s-1} O_{s-1}; v: six numbers per line, x_{s+1}(b, N - 1) and
+// X^T x_{s+1}).  O in its factored form acts line by line (it is block
+// diagonal over the lines), so its products are warp shuffles and warp sums;
+// the two triangular products of the forward step and W_s v cross lines,
+// through broadcast vectors in shared memory (double-buffered by step
+// parity).  Stage u < S: Linv_u and the O factors of record u; stage u >= S:
+// W_s of record s and the O factors of record s + 1, s = 2S - 2 - u.  Stage u
+// uses ring buffer u % P and mbarrier u % P with phase parity (u / P) & 1.  UPD: first r <- r - alpha q (written
 // back).  Writes the group's partial r.z (= |y|^2) and r.r.  A wait that runs
 // out sets err->flag and ends the slot after bounded waits for the copies in
 // flight.
@@ -896,7 +938,9 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
                                         unsigned long long lim, TnWait *__restrict__ err, double *__restrict__ part_rz,
                                         double *__restrict__ part_rr) {
   constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = 32 * G;
-  constexpr int LP = zlp(MG), RS = zg_rec(MG);
+  constexpr int LP = zlp(MG), RS = zg_rec(MG, G), WS = zg_ws(G), RSS = zg_stage<N, G>();
+  constexpr int LPX = LP + 8 * MG;  // forward stage: Linv_s and the O factors of record s
+  constexpr int BW = MG * WS;       // backward stage: W_s, then the O factors of record s + 1
   const int lt = threadIdx.x - 32 * w0, bid = 1 + w0;
   auto sync = [&]() {
     if (G == 1) __syncwarp();
@@ -919,29 +963,30 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   auto gidx = [&](int s) { return g0 + (size_t)s * gs; };
   const T *base = fac + gfac[grp];
   const int total = 2 * S;
-  int P = cap / RS;
+  int P = cap / RSS;
   P = P > kZgMaxStages ? kZgMaxStages : P;
   P = P > total ? total : P;
-  // stage sources: forward stage u = record u; backward stage u (slab
-  // s = 2S - 1 - u) = Linv_s of record s and the O factors of record s + 1
+  // stage sources: forward stage u = Linv and O factors of record u;
+  // backward stage u (slab s = 2S - 2 - u < S - 1) = W_s of record s and the
+  // O factors of record s + 1 (the last slab, s = S - 1, needs no stage)
+  const int total_st = 2 * S - 1;
   int issued = 0, ib = 0;  // stages issued so far and the ring buffer of the next (same in every thread)
   const T *src = base;     // lane 0: the next stage's (first) source
   auto issue_next = [&]() {
-    if (issued >= total) return;
+    if (issued >= total_st) return;
     const int u = issued++, b = ib;
     ib = ib + 1 == P ? 0 : ib + 1;
     if (lt == 0) {
-      T *dst = stage + (size_t)b * RS;
+      T *dst = stage + (size_t)b * RSS;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       if (u < S) {
-        mbar_expect(bars + b, (unsigned)(RS * sizeof(T)));
-        bulk_g2s(dst, src, (unsigned)(RS * sizeof(T)), bars + b);
-        src = u + 1 < S ? src + RS : src;  // the first backward stage is record S - 1 again
+        mbar_expect(bars + b, (unsigned)(LPX * sizeof(T)));
+        bulk_g2s(dst, src, (unsigned)(LPX * sizeof(T)), bars + b);
+        src = u + 1 < S ? src + RS : src - RS;  // then the backward stages from record S - 2 down
       } else {
-        const bool tail = u > S;  // slab s = 2S - 1 - u < S - 1: O factors of record s + 1
-        mbar_expect(bars + b, (unsigned)((tail ? RS : LP) * sizeof(T)));
-        bulk_g2s(dst, src, (unsigned)(LP * sizeof(T)), bars + b);
-        if (tail) bulk_g2s(dst + LP, src + RS + LP, (unsigned)((RS - LP) * sizeof(T)), bars + b);
+        mbar_expect(bars + b, (unsigned)((BW + 8 * MG) * sizeof(T)));
+        bulk_g2s(dst, src + LPX, (unsigned)(BW * sizeof(T)), bars + b);
+        bulk_g2s(dst + BW, src + RS + LP, (unsigned)(8 * MG * sizeof(T)), bars + b);
         src -= RS;
       }
     }
@@ -1027,10 +1072,10 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   // forward sweep
   T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
   T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
-  T w = T(0), ylast = T(0);
+  T w = T(0);
   for (int s = 0; s < S; ++s, ++at) {
     if (!wait()) { bad = true; break; }
-    const T *Ls = stage + (size_t)wb * RS, *XY = Ls + LP + 8 * t;
+    const T *Ls = stage + (size_t)wb * RSS, *XY = Ls + LP + 8 * t;
     wait_done();
     issue_next();  // every thread is past step s - 1: its buffer is free
     const int par = s & 1;
@@ -1062,46 +1107,45 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
     T y = lower(Ls, vb(par));
     if (!act) y = T(0);
     rz += y * y;
-    if (act) {
-      z[gidx(s)] = y;
-      vy(par)[lt] = y;
-    }
-    ylast = y;
+    if (act) vy(par)[lt] = y;
     sync();
     w = upper(Ls, vy(par));
     if (!act) w = T(0);
+    if (act) z[gidx(s)] = w;  // w_s, read back by the backward sweep
   }
-  // backward sweep
+  // backward sweep: x_{S-1} = w_{S-1} (already in z), then
+  // x_s = w_s - W_s v_{s+1}, v per line: x_{s+1}(b, N - 1) and X^T x_{s+1}
   if (!bad) {
-    T y0 = ylast;
-    T y1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
-    T y2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
-    T x = T(0);
-    for (int s = S - 1; s >= 0; --s, ++at) {
+    T x = w;
+    T w1 = (act && S > 1) ? z[gidx(S - 2)] : T(0);
+    T w2 = (act && S > 2) ? z[gidx(S - 3)] : T(0);
+    for (int s = S - 2; s >= 0; --s, ++at) {
       if (!wait()) { bad = true; break; }
-      const T *Ls = stage + (size_t)wb * RS, *XY = Ls + LP + 8 * t;
+      const T *Ws = stage + (size_t)wb * RSS, *XY = Ws + BW + 8 * t;
       wait_done();
       issue_next();
       const int par = s & 1;
-      T yv = y0;
-      y0 = y1;
-      y1 = y2;
-      if (act && s >= 3) y2 = z[gidx(s - 3)];
-      if (s + 1 < S) {  // yv -= (Linv_s O_s x_{s+1})_t
-        const T s0 = warp_allsum(act ? XY[0] * x : T(0));
-        const T s1 = warp_allsum(act ? XY[1] * x : T(0));
-        const T s2 = warp_allsum(act ? XY[2] * x : T(0));
-        T v = XY[4] * __shfl_sync(0xffffffffu, x, N - 1) + XY[5] * __shfl_sync(0xffffffffu, x, 2 * N - 1) +
-              XY[6] * __shfl_sync(0xffffffffu, x, 3 * N - 1);
-        if (k == 0) v += a == 0 ? s0 : (a == 1 ? s1 : s2);
-        if (act) vb(par)[lt] = v;
-        sync();
-        yv -= lower(Ls, vb(par));
-      }
-      if (act) vy(par)[lt] = yv;
+      const T wv = w1;
+      w1 = w2;
+      if (act && s >= 2) w2 = z[gidx(s - 2)];
+      const T e0 = __shfl_sync(0xffffffffu, x, N - 1);
+      const T e1 = __shfl_sync(0xffffffffu, x, 2 * N - 1);
+      const T e2 = __shfl_sync(0xffffffffu, x, 3 * N - 1);
+      const T c0 = warp_allsum(act ? XY[0] * x : T(0));
+      const T c1 = warp_allsum(act ? XY[1] * x : T(0));
+      const T c2 = warp_allsum(act ? XY[2] * x : T(0));
+      if (lane < 6) vb(par)[32 * li + lane] = lane < 3 ? (lane == 0 ? e0 : (lane == 1 ? e1 : e2))
+                                                      : (lane == 3 ? c0 : (lane == 4 ? c1 : c2));
       sync();
-      x = upper(Ls, vy(par));
-      if (!act) x = T(0);
+      const T *Wr = Ws + t * WS;
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < G; ++l) {
+        const T *vl = vb(par) + 32 * l;
+        acc += (Wr[6 * l] * vl[0] + Wr[6 * l + 1] * vl[1] + Wr[6 * l + 2] * vl[2]) +
+               (Wr[6 * l + 3] * vl[3] + Wr[6 * l + 4] * vl[4] + Wr[6 * l + 5] * vl[5]);
+      }
+      x = act ? wv - acc : T(0);
       if (act) z[gidx(s)] = x;
     }
   }
@@ -1471,7 +1515,7 @@ bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *p, char *
       const int start = p->ngroups;
       for (int i = 0; i < n; ++i) {
         if (hms[i]->N != N) continue;
-        const long long rec = zg_rec(g * 3 * N);
+        const long long rec = zg_rec(g * 3 * N, g);
         p->inst_start[(size_t)i * 5 + g] = p->ngroups;
         for (const auto &mm : per[i]) {
           if ((int)mm.size() != g) continue;
@@ -1479,6 +1523,7 @@ bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *p, char *
           p->inst.push_back(i);
           p->fac_off.push_back(p->nfac);
           p->nfac += (long long)hms[i]->nslab * rec;
+          p->ncompact += (long long)hms[i]->nslab * (zlp(g * 3 * N) + 8 * g * 3 * N);
           ++p->inst_n[(size_t)i * 5 + g];
           ++p->ngroups;
         }

@@ -40,6 +40,7 @@ struct ZGroupPlan {
   std::vector<int> inst;            // per group: mirror
   std::vector<long long> fac_off;   // per group: first factor entry
   long long nfac = 0;               // factor entries in all
+  long long ncompact = 0;           // of which Linv_s and the O factors (the rest: W_s)
   int ncls = 0;
   int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
   std::vector<int> inst_start, inst_n;  // [mirror * 5 + g]: first group and count of size g (set-up)
