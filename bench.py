@@ -658,7 +658,7 @@ def main():
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
     if pc == "zgroup":
-        zkernel = (f"zgroup_packed_kernel<{'N' if batched else N},float,0>"
+        zkernel = (f"zgroup_packed_kernel<{'N' if batched else N},float>"
                    + (", one launch per degree" if batched else ""))
     else:
         zkernel = ("zline_solve_batch_kernel<N,float,float,0>" if batched
@@ -685,7 +685,7 @@ def main():
                      "frac": zbytes / tz / 1e9 / hbm_peak,
                      "traffic": ZLINE_TRAFFIC.get((args.workload, zkernel)),
                      "kernel": zkernel, "us": tz * 1e6, "us_eager": tz_eager * 1e6, "timing": tz_how,
-                     "algorithmic_bytes": zbytes, "bytes": "compact FP32 factors (Linv_s, O_s) once + r in + z out",
+                     "algorithmic_bytes": zbytes, "bytes": "compact FP32 factors (S_s^-1 packed, O_s factors) once + r in + z out",
                      "peak_source": peak_src},
         "roofline_apply": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
                            "frac": achieved / peak_fp32,

@@ -194,9 +194,10 @@ tn_status tn_precond_apply(tn_ctx *ctx, int precond, int precision, const void *
 
 /* Bytes of FP32 factors one FP32 application of `precond` must read at
  * least (building the factors first if needed), for bandwidth accounting:
- * TN_PC_ZLINE the line records; TN_PC_ZGROUP the compact factors Linv_s and
- * O_s (the records' backward couplings W_s, which derive from them, are not
- * counted); TN_PC_JACOBI the inverse diagonal.  *bytes: host. */
+ * TN_PC_ZLINE the line records; TN_PC_ZGROUP the compact factors, S_s^-1
+ * (packed symmetric) and the factored couplings O_s (the records' backward
+ * couplings W_s, which derive from them, are not counted); TN_PC_JACOBI the
+ * inverse diagonal.  *bytes: host. */
 tn_status tn_precond_factor_bytes(tn_ctx *ctx, int precond, long long *bytes);
 
 /* Krylov solve of A u = b for the beam load (Sec. 2.3).

@@ -380,6 +380,7 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
   g.inst = is_batch(c) ? c->d_ginst : nullptr;
   g.meshes = is_batch(c) ? c->batch->d_meshes : nullptr;
   g.dof_off = is_batch(c) ? c->batch->d_dof_off : nullptr;
+  g.ndof = (long long)c->ndof;
   g.ngroups = p.ngroups;
   g.ncls = p.ncls;
   for (int k = 0; k < p.ncls; ++k) {

@@ -686,15 +686,16 @@ __global__ void zgroup_cross_kernel(const DevMesh m, double *__restrict__ xblk) 
   }
 }
 
-// Group record of slab s: [Linv_s packed by columns (zlp(MG)) | O_{s-1} in
-// factored form (8 MG)].  The coupling block O_{s-1} (rows: slab s - 1,
+// Group record of slab s: [S_s^{-1} packed by columns (lower triangle,
+// zlp(MG)) | O_{s-1} in factored form (8 MG) | W_s], S_s = L_s L_s^T the
+// slab's Schur complement of the block Cholesky (S_s^{-1} = Linv_s^T Linv_s).  The coupling block O_{s-1} (rows: slab s - 1,
 // columns: slab s, block diagonal over the lines) is nonzero only in the
 // rows of the bottom-face nodes (k = 0) and the columns of the top-face
 // nodes (k2 = N - 1) of each line (Eqs. (numflux), (penalty) on the zeta
 // face), so O = E_0 X^T + Y E_{N-1}^T with per row t: X[t][a] = O[(a, 0), t]
 // and Y[t][b] = O[t, (b, N - 1)] (Y zero on k = 0 rows).  Row t stores
-// X[t][0..2], 0, Y[t][0..2], 0.  The solve applies Z_s = Linv_{s-1} O_{s-1}
-// through Linv and these factors instead of storing Z densely.
+// X[t][0..2], 0, Y[t][0..2], 0.  The solve applies the coupling through
+// these factors instead of storing Z_s = Linv_{s-1} O_{s-1} densely.
 // The record ends with the backward sweep's coupling W_s = S_s^{-1} [Y_s | E_0]
 // (MG x 6G, rows padded to zg_ws(G)), S_s = L_s L_s^T the slab's Schur
 // complement and Y_s, E_0 of O_s (the coupling to slab s + 1): per line l,
@@ -707,7 +708,7 @@ __host__ __device__ constexpr int zg_rec(int MG, int G) { return zlp(MG) + 8 * M
 
 // block Cholesky along the slabs of one group (one CTA; FP64 working
 // matrices G, Linv, Z of (3 g N)^2 entries each in `work`), then FP32 and
-// FP64 records [Linv_s packed | Z_s] as for single lines
+// FP64 records [S_s^{-1} packed | O_{s-1} factors | W_s]
 template <int N>
 __global__ void __launch_bounds__(128)
 zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
@@ -795,12 +796,14 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
     __syncthreads();
     float *Lf = fac + rec0 + (long long)s * RS;
     double *Ld = fac64 + rec0 + (long long)s * RS;
-    for (int q = tid; q < MG * MG; q += nth) {
+    for (int q = tid; q < MG * MG; q += nth) {  // S^{-1} = Linv^T Linv, lower triangle
       const int r = q / MG, cc = q - r * MG;
       if (r >= cc) {
+        double acc = 0.0;
+        for (int p = r; p < MG; ++p) acc += Li[p * MG + r] * Li[p * MG + cc];
         const int pi = zcol(MG, cc) + r - cc;
-        Ld[pi] = Li[q];
-        Lf[pi] = (float)Li[q];
+        Ld[pi] = acc;
+        Lf[pi] = (float)acc;
       }
     }
     for (int q = MG * (MG + 1) / 2 + tid; q < LP; q += nth) { Lf[q] = 0.0f; Ld[q] = 0.0; }
@@ -871,7 +874,7 @@ constexpr int kZgMaxStages = 8;
 // (4 lines) across the four warps of a CTA, so that six CTAs (FP32, N = 7)
 // share an SM; smaller groups fit more stages in the same room
 // stage buffer of a group of G lines: the larger of the forward stage
-// (Linv_s and the O factors of record s) and the backward stage (W_s and
+// (S_s^{-1} and the O factors of record s) and the backward stage (W_s and
 // the O factors of record s + 1)
 template <int N, int G>
 __host__ __device__ constexpr int zg_stage() {
@@ -918,28 +921,29 @@ __device__ __forceinline__ double warp_allsum(double v) {
 // line li of the group is warp w0 + li, its rows (a, k) lanes a N + k < 3N:
 //   forward   y_s = Linv_s (r_s - O_{s-1}^T w_{s-1}),  w_s = Linv_s^T y_s
 //   backward  x_s = Linv_s^T (y_s - Linv_s O_s x_{s+1}) = w_s - W_s v_{s+1}
-// (Z_s = Linv_{s-1} O_{s-1}; v: six numbers per line, x_{s+1}(b, N - 1) and
-// X^T x_{s+1}).  O in its factored form acts line by line (it is block
-// diagonal over the lines), so its products are warp shuffles and warp sums;
-// the two triangular products of the forward step and W_s v cross lines,
-// through broadcast vectors in shared memory (double-buffered by step
-// parity).  Stage u < S: Linv_u and the O factors of record u; stage u >= S:
+// (v: six numbers per line, x_{s+1}(b, N - 1) and X^T x_{s+1}).  The forward
+// step forms w_s = S_s^{-1} b_s, b_s = r_s - O_{s-1}^T w_{s-1}, in one
+// symmetric product, and r.z = sum_s |y_s|^2 = sum_s b_s . w_s.  O in its
+// factored form acts line by line (it is block diagonal over the lines), so
+// its products are warp shuffles and warp sums; S_s^{-1} b_s and W_s v cross
+// lines, through broadcast vectors in shared memory (double-buffered by step
+// parity).  Stage u < S: S_u^{-1} and the O factors of record u; stage u >= S:
 // W_s of record s and the O factors of record s + 1, s = 2S - 2 - u.  Stage u
-// uses ring buffer u % P and mbarrier u % P with phase parity (u / P) & 1.  UPD: first r <- r - alpha q (written
-// back).  Writes the group's partial r.z (= |y|^2) and r.r.  A wait that runs
+// uses ring buffer u % P and mbarrier u % P with phase parity (u / P) & 1.
+// Writes the group's partial r.z (= |y|^2) and r.r.  A wait that runs
 // out sets err->flag and ends the slot after bounded waits for the copies in
 // flight.
-template <int N, int G, typename T, bool UPD>
-__device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__restrict__ r,
-                                        const T *__restrict__ q, T *__restrict__ z, const int4 *__restrict__ glines,
-                                        const long long *__restrict__ gfac, const T *__restrict__ fac, T al,
+template <int N, int G, typename T>
+__device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, const T *__restrict__ r,
+                                        T *__restrict__ z, const int4 *__restrict__ glines,
+                                        const long long *__restrict__ gfac, const T *__restrict__ fac,
                                         T *__restrict__ stage, int cap, T *__restrict__ vecs,
                                         unsigned long long *__restrict__ bars, double *__restrict__ psum,
                                         unsigned long long lim, TnWait *__restrict__ err, double *__restrict__ part_rz,
                                         double *__restrict__ part_rr) {
   constexpr int M = 3 * N, N2 = N * N, n = N * N * N, MG = G * M, NT = 32 * G;
   constexpr int LP = zlp(MG), RS = zg_rec(MG, G), WS = zg_ws(G), RSS = zg_stage<N, G>();
-  constexpr int LPX = LP + 8 * MG;  // forward stage: Linv_s and the O factors of record s
+  constexpr int LPX = LP + 8 * MG;  // forward stage: S_s^{-1} and the O factors of record s
   constexpr int BW = MG * WS;       // backward stage: W_s, then the O factors of record s + 1
   const int lt = threadIdx.x - 32 * w0, bid = 1 + w0;
   auto sync = [&]() {
@@ -952,9 +956,8 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   const int t = li * M + (act ? lane : 0);  // row of the group's blocks
   const int a = (act ? lane : 0) / N, k = (act ? lane : 0) - a * N;
   // broadcast vectors hold line lj's M entries at 32 lj (16-byte aligned)
-  T *const vbuf = vecs + 4 * 32 * w0;  // [2 parities][vb, vy][32 G]
+  T *const vbuf = vecs + 4 * 32 * w0;  // [2 parities][vb][32 G] (room for 2 x 2 x 32 G)
   auto vb = [&](int par) { return vbuf + par * 2 * NT; };
-  auto vy = [&](int par) { return vbuf + par * 2 * NT + NT; };
   const int4 L4 = glines[grp];
   const int lid = li == 0 ? L4.x : (li == 1 ? L4.y : (li == 2 ? L4.z : L4.w));
   const int c = lid / N2, qn = lid - c * N2;
@@ -966,7 +969,7 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   int P = cap / RSS;
   P = P > kZgMaxStages ? kZgMaxStages : P;
   P = P > total ? total : P;
-  // stage sources: forward stage u = Linv and O factors of record u;
+  // stage sources: forward stage u = S_u^{-1} and O factors of record u;
   // backward stage u (slab s = 2S - 2 - u < S - 1) = W_s of record s and the
   // O factors of record s + 1 (the last slab, s = S - 1, needs no stage)
   const int total_st = 2 * S - 1;
@@ -1017,61 +1020,45 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
   bool bad = false;
   int at = 0;  // the stage being waited for
   const int pl = zcol(MG, t) - t;
-  // the products line block by line block, the block index a compile-time
-  // constant so that every packed offset folds: (Linv v)_t takes the blocks
-  // before this thread's line in full and its own block up to the diagonal
-  // (blocks after it are zero); (Linv^T v)_t its own block from the diagonal
-  // and the blocks after it in full
+  // w = S^{-1} v, line block by line block, the block index a compile-time
+  // constant so that every packed offset folds: row t of the symmetric
+  // S^{-1} is the stored lower triangle's row t (blocks before this thread's
+  // line, and its own block up to the diagonal) followed by its column t
+  // (its own block below the diagonal, and the blocks after it)
   const int tl = act ? lane : 0;  // row within the line
-  auto lblock = [&](const T *Ls, const T *v, auto LJ, bool diag) {
+  auto lblock = [&](const T *Ls, const T *v, auto LJ) {
+    constexpr int c0 = decltype(LJ)::value * M;
+    return bcast_dot<M, T>(v + 32 * decltype(LJ)::value,
+                           [&](int cc) { return Ls[zcol(MG, c0 + cc) + t - c0 - cc]; });
+  };
+  auto ublock = [&](const T *Ls, const T *v, auto LJ) {
+    constexpr int c0 = decltype(LJ)::value * M;
+    return bcast_dot<M, T>(v + 32 * decltype(LJ)::value, [&](int cc) { return Ls[pl + c0 + cc]; });
+  };
+  auto dblock = [&](const T *Ls, const T *v, auto LJ) {
     constexpr int c0 = decltype(LJ)::value * M;
     return bcast_dot<M, T>(v + 32 * decltype(LJ)::value, [&](int cc) {
-      return (!diag || cc <= tl) ? Ls[zcol(MG, c0 + cc) + t - c0 - cc] : T(0);
+      return cc <= tl ? Ls[zcol(MG, c0 + cc) + t - c0 - cc] : Ls[pl + c0 + cc];
     });
   };
-  auto ublock = [&](const T *Ls, const T *v, auto LJ, bool diag) {
-    constexpr int c0 = decltype(LJ)::value * M;
-    return bcast_dot<M, T>(v + 32 * decltype(LJ)::value, [&](int cc) {
-      return (!diag || cc >= tl) ? Ls[pl + c0 + cc] : T(0);
-    });
-  };
-  using L0 = std::integral_constant<int, 0>;
-  using L1 = std::integral_constant<int, (G > 1 ? 1 : 0)>;
-  using L2 = std::integral_constant<int, (G > 2 ? 2 : 0)>;
-  using L3 = std::integral_constant<int, (G > 3 ? 3 : 0)>;
-  auto lower = [&](const T *Ls, const T *v) {
+  auto symrow = [&](const T *Ls, const T *v) {
     T acc = T(0);
-    if (li == 0) acc = lblock(Ls, v, L0{}, true);
-    if (G > 1 && li == 1) acc = lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, true);
-    if (G > 2 && li == 2) acc = (lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, false)) + lblock(Ls, v, L2{}, true);
-    if (G > 3 && li == 3)
-      acc = (lblock(Ls, v, L0{}, false) + lblock(Ls, v, L1{}, false)) +
-            (lblock(Ls, v, L2{}, false) + lblock(Ls, v, L3{}, true));
-    return acc;
-  };
-  auto upper = [&](const T *Ls, const T *v) {
-    T acc = T(0);
-    if (li == 0) {
-      acc = ublock(Ls, v, L0{}, true);
-      if (G > 1) acc += ublock(Ls, v, L1{}, false);
-      if (G > 2) acc += ublock(Ls, v, L2{}, false);
-      if (G > 3) acc += ublock(Ls, v, L3{}, false);
-    }
-    if (G > 1 && li == 1) {
-      acc = ublock(Ls, v, L1{}, true);
-      if (G > 2) acc += ublock(Ls, v, L2{}, false);
-      if (G > 3) acc += ublock(Ls, v, L3{}, false);
-    }
-    if (G > 2 && li == 2) {
-      acc = ublock(Ls, v, L2{}, true);
-      if (G > 3) acc += ublock(Ls, v, L3{}, false);
-    }
-    if (G > 3 && li == 3) acc = ublock(Ls, v, L3{}, true);
+    auto part = [&](auto LJ) {
+      constexpr int J = decltype(LJ)::value;
+      if (J >= G) return;
+      if (J < li) acc += lblock(Ls, v, LJ);
+      else if (J == li) acc += dblock(Ls, v, LJ);
+      else acc += ublock(Ls, v, LJ);
+    };
+    part(std::integral_constant<int, 0>{});
+    part(std::integral_constant<int, 1>{});
+    part(std::integral_constant<int, 2>{});
+    part(std::integral_constant<int, 3>{});
     return acc;
   };
   // forward sweep
-  T r0 = act ? r[gidx(0)] : T(0), q0 = (UPD && act) ? q[gidx(0)] : T(0);
-  T r1 = (act && S > 1) ? r[gidx(1)] : T(0), q1 = (UPD && act && S > 1) ? q[gidx(1)] : T(0);
+  T r0 = act ? r[gidx(0)] : T(0);
+  T r1 = (act && S > 1) ? r[gidx(1)] : T(0);
   T w = T(0);
   for (int s = 0; s < S; ++s, ++at) {
     if (!wait()) { bad = true; break; }
@@ -1079,17 +1066,9 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
     wait_done();
     issue_next();  // every thread is past step s - 1: its buffer is free
     const int par = s & 1;
-    T rv = r0;
-    if (UPD) {
-      rv -= al * q0;
-      if (act) r[gidx(s)] = rv;
-    }
+    const T rv = r0;
     r0 = r1;
-    q0 = q1;
-    if (act && s + 2 < S) {
-      r1 = r[gidx(s + 2)];
-      if (UPD) q1 = q[gidx(s + 2)];
-    }
+    if (act && s + 2 < S) r1 = r[gidx(s + 2)];
     rr += rv * rv;
     T bv = rv;
     if (s > 0) {  // bv -= (O_{s-1}^T w_{s-1})_t, line by line
@@ -1104,14 +1083,10 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, T *__
     }
     if (act) vb(par)[lt] = bv;
     sync();
-    T y = lower(Ls, vb(par));
-    if (!act) y = T(0);
-    rz += y * y;
-    if (act) vy(par)[lt] = y;
-    sync();
-    w = upper(Ls, vy(par));
+    w = symrow(Ls, vb(par));  // w_s = S_s^{-1} bv = Linv_s^T y_s
     if (!act) w = T(0);
-    if (act) z[gidx(s)] = w;  // w_s, read back by the backward sweep
+    rz += bv * w;             // |y_s|^2
+    if (act) z[gidx(s)] = w;  // read back by the backward sweep
   }
   // backward sweep: x_{S-1} = w_{S-1} (already in z), then
   // x_s = w_s - W_s v_{s+1}, v per line: x_{s+1}(b, N - 1) and X^T x_{s+1}
@@ -1226,14 +1201,13 @@ __device__ void fold_beta(const PcgFold &f) {
 // (largest first); the last CTA to finish resets queue[0..1] for the next
 // launch.  One mesh (ginst == nullptr) or a batch (per group: its mirror's
 // mesh and first unknown).
-template <int N, typename T, bool UPD>
-__global__ void __launch_bounds__(kZgThreads)
+template <int N, typename T>
+__global__ void __launch_bounds__(kZgThreads, 4)
 zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevMesh *__restrict__ meshes,
                      const long long *__restrict__ dof_off, const int4 *__restrict__ glines,
                      const long long *__restrict__ gfac, const int4 *__restrict__ packs, int pk0, int npk,
-                     int *__restrict__ queue, const T *__restrict__ fac, T *__restrict__ r,
-                     const T *__restrict__ q, T *__restrict__ z, const double *__restrict__ alpha,
-                     double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
+                     int *__restrict__ queue, const T *__restrict__ fac, const T *__restrict__ r,
+                     T *__restrict__ z, double *__restrict__ part_rz, double *__restrict__ part_rr, const int *__restrict__ done,
                      TnWait *__restrict__ err, const PcgFold fold) {
   if (done && *done) return;
   constexpr int SW = zg_stage_per_warp<N, T>();
@@ -1245,7 +1219,6 @@ zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevM
   __shared__ double psum[8];
   const int warp = threadIdx.x >> 5;
   const unsigned long long lim = wait_limit(err);
-  const T al = UPD ? (T)*alpha : T(0);
   for (;;) {
     if (threadIdx.x == 0) s_pk = atomicAdd(queue, 1);
     __syncthreads();
@@ -1270,8 +1243,8 @@ zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevM
     }
     if (grp >= 0) {
       int mncol = m1.ncol, mslab = m1.nslab;
-      T *rg = r, *zg = z;
-      const T *qg = q;
+      const T *rg = r;
+      T *zg = z;
       if (ginst) {
         const int in = ginst[grp];
         mncol = meshes[in].ncol;
@@ -1279,26 +1252,25 @@ zgroup_packed_kernel(const DevMesh m1, const int *__restrict__ ginst, const DevM
         const long long o = dof_off[in];
         rg += o;
         zg += o;
-        if (UPD) qg += o;
       }
       T *stg = stage0 + (size_t)w0 * SW;
       unsigned long long *sb = bars + kZgMaxStages * w0;
       const int cap = G * SW;
       switch (G) {
         case 1:
-          zg_slot<N, 1, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+          zg_slot<N, 1, T>(grp, w0, mncol, mslab, rg, zg, glines, gfac, fac, stg, cap, vecs, sb, psum,
                                 lim, err, part_rz, part_rr);
           break;
         case 2:
-          zg_slot<N, 2, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+          zg_slot<N, 2, T>(grp, w0, mncol, mslab, rg, zg, glines, gfac, fac, stg, cap, vecs, sb, psum,
                                 lim, err, part_rz, part_rr);
           break;
         case 3:
-          zg_slot<N, 3, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+          zg_slot<N, 3, T>(grp, w0, mncol, mslab, rg, zg, glines, gfac, fac, stg, cap, vecs, sb, psum,
                                 lim, err, part_rz, part_rr);
           break;
         default:
-          zg_slot<N, 4, T, UPD>(grp, w0, mncol, mslab, rg, qg, zg, glines, gfac, fac, al, stg, cap, vecs, sb, psum,
+          zg_slot<N, 4, T>(grp, w0, mncol, mslab, rg, zg, glines, gfac, fac, stg, cap, vecs, sb, psum,
                                 lim, err, part_rz, part_rr);
           break;
       }
@@ -1407,12 +1379,12 @@ cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, int inst, cons
 
 // persistent: as many CTAs as fit at once, never more than packs.  grid == 0:
 // only compute the grid into *grid_out; else launch with it.
-template <int N, typename T, bool UPD>
-cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const void *fac, void *r, const void *q,
-                            void *z, const double *alpha, double *prz, double *prr, const int *done, TnWait *zerr,
-                            cudaStream_t st, const PcgFold &fold, int *grid_out) {
+template <int N, typename T>
+cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const void *fac, const void *r, void *z,
+                            double *prz, double *prr, const int *done, TnWait *zerr, cudaStream_t st,
+                            const PcgFold &fold, int *grid_out) {
   constexpr size_t sm = zg_smem<N, T>();
-  auto kern = zgroup_packed_kernel<N, T, UPD>;
+  auto kern = zgroup_packed_kernel<N, T>;
   cudaError_t err = zline_smem_optin(kern, sm);
   if (err != cudaSuccess) return err;
   static int per_sm[64] = {0};
@@ -1436,24 +1408,29 @@ cudaError_t zgroup_launch_t(const DevMesh &m, const ZGroupDev &gd, int k, const 
     return cudaSuccess;
   }
   kern<<<grid, kZgThreads, sm, st>>>(m, gd.inst, gd.meshes, gd.dof_off, gd.lines, gd.fac_off, gd.packs,
-                                     gd.pk_start[k], gd.pk_n[k], gd.queue + 2 * k, (const T *)fac, (T *)r,
-                                     (const T *)q, (T *)z, alpha, prz, prr, done, zerr, fold);
+                                     gd.pk_start[k], gd.pk_n[k], gd.queue + 2 * k, (const T *)fac, (const T *)r,
+                                     (T *)z, prz, prr, done, zerr, fold);
   return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int k, int prec, const void *fac, void *r,
-                            const void *q, void *z, const double *alpha, double *prz, double *prr,
-                            const int *done, TnWait *zerr, cudaStream_t st, const PcgFold &fold, int *grid_out) {
+cudaError_t zgroup_launch_n(const DevMesh &m, const ZGroupDev &gd, int k, int prec, const void *fac, const void *r,
+                            void *z, double *prz, double *prr, const int *done, TnWait *zerr, cudaStream_t st,
+                            const PcgFold &fold, int *grid_out) {
   if (prec == TN_F64)
-    return q ? zgroup_launch_t<N, double, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
-                                                grid_out)
-             : zgroup_launch_t<N, double, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
-                                                 grid_out);
-  return q ? zgroup_launch_t<N, float, true>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
-                                             grid_out)
-           : zgroup_launch_t<N, float, false>(m, gd, k, fac, r, q, z, alpha, prz, prr, done, zerr, st, fold,
-                                              grid_out);
+    return zgroup_launch_t<N, double>(m, gd, k, fac, r, z, prz, prr, done, zerr, st, fold, grid_out);
+  return zgroup_launch_t<N, float>(m, gd, k, fac, r, z, prz, prr, done, zerr, st, fold, grid_out);
+}
+
+// r -= alpha q ahead of the grouped-line solve (the PCG residual update; a
+// separate pass measured faster than the update fused into the line walk)
+template <typename T>
+__global__ void zgroup_rupdate_kernel(long long n, T *__restrict__ r, const T *__restrict__ q,
+                                      const double *__restrict__ alpha, const int *__restrict__ done) {
+  if (done && *done) return;
+  const T al = (T)*alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] -= al * q[i];
 }
 
 }  // namespace
@@ -1623,8 +1600,7 @@ cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, con
       switch (gd.pk_N[k]) {
 #define TN_CASE(NN)                                                                                              \
         case NN:                                                                                                \
-          err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, st, fold, \
-                                    &g);                                                                        \
+          err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, z, part_rz, part_rr, done, zerr, st, fold, &g); \
           break;
         TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
@@ -1632,6 +1608,15 @@ cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, con
       }
       fold.total += g;
     }
+    if (err != cudaSuccess) return err;
+  }
+  if (q) {  // the residual update, before every degree class reads r
+    const int blocks = 4 * tn_sm_count();
+    if (prec == TN_F64)
+      zgroup_rupdate_kernel<double><<<blocks, 256, 0, st>>>(gd.ndof, (double *)r, (const double *)q, alpha, done);
+    else
+      zgroup_rupdate_kernel<float><<<blocks, 256, 0, st>>>(gd.ndof, (float *)r, (const float *)q, alpha, done);
+    err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   if (gd.npk > 1) err = cudaEventRecord(gd.fork, st);
@@ -1650,8 +1635,7 @@ cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, con
     switch (gd.pk_N[k]) {
 #define TN_CASE(NN)                                                                                        \
       case NN:                                                                                            \
-        err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, q, z, alpha, part_rz, part_rr, done, zerr, sk, fold, \
-                                  nullptr);                                                                 \
+        err = zgroup_launch_n<NN>(one, gd, k, prec, fac, r, z, part_rz, part_rr, done, zerr, sk, fold, nullptr); \
         break;
       TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE

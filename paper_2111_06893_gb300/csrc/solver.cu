@@ -6,9 +6,12 @@
 // the fused operator apply (which also returns p.Ap per element), a
 // one-block reduction for alpha, a fused vector update (x, r, z = D^-1 r,
 // partial r.z and r.r), a one-block reduction for beta and the direction
-// update.  With the column-line preconditioner the residual update r -= alpha
-// q runs inside the line solve (which also returns partial r.z and r.r) and
-// the solution update x += alpha p inside the direction update.  A chunk of
+// update.  With the single-line preconditioner the residual update r -= alpha
+// q runs inside the line solve (which also returns partial r.z and r.r);
+// with grouped lines it is a launch of its own ahead of the solve (measured
+// faster than fused there), and alpha and beta fold into the apply and the
+// solve, four launches per iteration.  The solution update x += alpha p runs
+// inside the direction update.  A chunk of
 // iterations is recorded once in a CUDA graph and replayed.  Krylov scalars
 // live on the device; once converged every kernel returns immediately, so a
 // replayed chunk never runs past convergence.  The host reads a small status
@@ -419,8 +422,8 @@ template <typename T>
 static cudaError_t pcg_iteration_zline(const OpSys &sys, int prec, size_t n, PcgVectors &v, tn_pcg_scalars *s,
                                        double *part_elem, double *part_red, cudaStream_t st) {
   if (sys.grouped && sys.fold_cnt) {
-    // three launches: the apply with the alpha step, the grouped-line solve
-    // with the residual update and the beta step, the direction update
+    // four launches: the apply with the alpha step, the residual update,
+    // the grouped-line solve with the beta step, the direction update
     PcgFold fa;
     fa.s = s;
     fa.cnt = sys.fold_cnt;
@@ -531,7 +534,7 @@ static cudaError_t pcg_run(const OpSys &sys, int prec, size_t n, PcgVectors &v, 
   double best = INFINITY;
   int stall = 0;
   for (;;) {
-    g_launches += (zl && sys.grouped && sys.fold_cnt ? 3LL : 5LL) * chunk;
+    g_launches += (zl && sys.grouped && sys.fold_cnt ? 4LL : (zl && sys.grouped ? 6LL : 5LL)) * chunk;
     err = cudaGraphLaunch(exec, st);
     if (err != cudaSuccess) break;
     err = cudaMemcpyAsync(s_host, s_dev, sizeof(tn_pcg_scalars), cudaMemcpyDeviceToHost, st);

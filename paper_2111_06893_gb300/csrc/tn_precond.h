@@ -57,6 +57,7 @@ struct ZGroupDev {
   const int *inst = nullptr;           // batch: mirror of every group (nullptr: one mesh)
   const DevMesh *meshes = nullptr;     // batch: meshes of the mirrors (device)
   const long long *dof_off = nullptr;  // batch: first unknown of every mirror (device)
+  long long ndof = 0;                  // unknowns of the mesh or of the whole batch
   int ngroups = 0, ncls = 0;
   int cls_N[kZgMaxCls] = {0}, cls_G[kZgMaxCls] = {0}, cls_start[kZgMaxCls] = {0}, cls_n[kZgMaxCls] = {0};
   const int4 *packs = nullptr;         // the plan's packs (device)
@@ -75,7 +76,8 @@ cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, con
                             const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
                             double *fac64, int *status, cudaStream_t st);
 // as tn_zline_solve, over the groups (m: the mesh, nullptr for a batch);
-// partial sums: one per group
+// partial sums: one per group.  q != nullptr: r -= alpha q first, as a
+// launch of its own over all gd.ndof unknowns
 // fold (optional): the beta step of a PCG iteration (s and cnt; the rest is
 // filled in here)
 cudaError_t tn_zgroup_solve(const DevMesh *m, const ZGroupDev &gd, int prec, const void *fac, void *r,
