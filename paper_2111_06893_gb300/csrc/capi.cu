@@ -402,8 +402,8 @@ static tn_status ensure_zgroup(tn_ctx *c, cudaStream_t st) {
     e = cudaMemcpyAsync(c->d_ginst, p.inst.data(), sizeof(int) * p.ngroups, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->gstatus, 0, 2 * sizeof(int), st);
   for (int i = 0; i < n && e == cudaSuccess; ++i)  // one mirror after another (shared set-up scratch)
-    e = tn_zgroup_setup(dms[i], p, i, c->d_glines, c->d_gfac_off, blk, xblk, work, c->gfac, c->gfac64, c->gstatus,
-                        st);
+    e = tn_zgroup_setup(dms[i], p, c->zgd, i, c->d_glines, c->d_gfac_off, blk, xblk, work, c->gfac, c->gfac64,
+                        c->gstatus, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, c->gstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(blk); dfree(xblk); dfree(work);

@@ -707,8 +707,9 @@ __host__ __device__ constexpr int zg_ws(int G) { return pad4(6 * G); }
 __host__ __device__ constexpr int zg_rec(int MG, int G) { return zlp(MG) + 8 * MG + MG * zg_ws(G); }
 
 // block Cholesky along the slabs of one group (one CTA; FP64 working
-// matrices G, Linv, Z of (3 g N)^2 entries each in `work`), then FP32 and
-// FP64 records [S_s^{-1} packed | O_{s-1} factors | W_s]
+// matrices G and Linv of (3 g N)^2 entries each and the (6 g)^2 C in
+// `work`), then FP32 and FP64 records [S_s^{-1} packed | O_{s-1} factors |
+// W_s]
 template <int N>
 __global__ void __launch_bounds__(128)
 zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const long long *__restrict__ gfac,
@@ -719,7 +720,7 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
   const int grp = gbase + blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int MG = g * M, S = m.nslab;
   const int LP = zlp(MG), RS = zg_rec(MG, g), WS = zg_ws(g);
-  double *Gm = work + (size_t)blockIdx.x * 3 * MG * MG, *Li = Gm + MG * MG, *Z = Li + MG * MG;
+  double *Gm = work + (size_t)blockIdx.x * 3 * MG * MG, *Li = Gm + MG * MG, *Cm = Li + MG * MG;
   __shared__ int lid[4], xof[4][4];
   if (tid < 4) {
     const int4 L4 = glines[grp];
@@ -747,7 +748,28 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
   __syncthreads();
   const long long rec0 = gfac[grp];
   for (int s = 0; s < S; ++s) {
-    // diagonal block of slab s (line blocks, cross-line face blocks) minus Z_s^T Z_s
+    // Schur complement of slab s: the diagonal block (line blocks, cross-line
+    // face blocks) minus O_{s-1}^T S_{s-1}^{-1} O_{s-1}.  With O_{s-1} = U V^T,
+    // U = [Y | E_0] (slab s - 1) and V = [E_{N-1} | X] (slab s), columns
+    // paired as in W_{s-1} = S_{s-1}^{-1} U, that is V C V^T with the 6g x 6g
+    // C = U^T W_{s-1}; a row of V has at most four nonzeros
+    const int G6 = 6 * g;
+    if (s > 0) {
+      const double *Wp = fac64 + rec0 + (long long)(s - 1) * RS + LP + 8 * MG;
+      for (int q = tid; q < G6 * G6; q += nth) {
+        const int i = q / G6, j = q - i * G6, l = i / 6, ii = i - l * 6;
+        double acc = 0.0;
+        if (ii < 3) {  // Y of component b = ii: O_{s-1}[p, (b, N - 1)] on the rows p of line l with k != 0
+          const double *O = blk + (((size_t)lid[l] * S + (s - 1)) * 2 + 1) * M * M;
+          for (int pl = 0; pl < M; ++pl)
+            if (pl % N != 0) acc += O[pl * M + ii * N + (N - 1)] * Wp[(size_t)(l * M + pl) * WS + j];
+        } else {  // E_0: row (a, k = 0) of line l
+          acc = Wp[(size_t)(l * M + (ii - 3) * N) * WS + j];
+        }
+        Cm[q] = acc;
+      }
+      __syncthreads();
+    }
     for (int q = tid; q < MG * MG; q += nth) {
       const int r = q / MG, cc = q - r * MG, t1 = r / M, t2 = cc / M, rr = r - t1 * M, c2 = cc - t2 * M;
       double v = 0.0;
@@ -757,8 +779,26 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
         const size_t e = (size_t)s * m.ncol + lid[t1] / N2;
         v = xblk[(e * 4 * N + xof[t1][t2]) * M * M + rr * M + c2];
       }
-      if (s > 0)
-        for (int p = 0; p < MG; ++p) v -= Z[p * MG + r] * Z[p * MG + cc];
+      if (s > 0) {  // the nonzeros of V's rows r and cc: (column, value)
+        int ir[4], ic[4];
+        double vr[4], vc[4];
+        int nr = 0, nc = 0;
+        const double *Or = blk + (((size_t)lid[t1] * S + (s - 1)) * 2 + 1) * M * M;
+        const double *Oc = blk + (((size_t)lid[t2] * S + (s - 1)) * 2 + 1) * M * M;
+        if (rr % N == N - 1) { ir[nr] = 6 * t1 + rr / N; vr[nr++] = 1.0; }
+        if (c2 % N == N - 1) { ic[nc] = 6 * t2 + c2 / N; vc[nc++] = 1.0; }
+        for (int a = 0; a < 3; ++a) {
+          ir[nr] = 6 * t1 + 3 + a; vr[nr++] = Or[(a * N) * M + rr];  // X[r][a] = O_{s-1}[(a, 0), r]
+          ic[nc] = 6 * t2 + 3 + a; vc[nc++] = Oc[(a * N) * M + c2];
+        }
+        double sum = 0.0;
+        for (int x = 0; x < nr; ++x) {
+          double row = 0.0;
+          for (int y = 0; y < nc; ++y) row += Cm[ir[x] * G6 + ic[y]] * vc[y];
+          sum += vr[x] * row;
+        }
+        v -= sum;
+      }
       Gm[q] = v;
     }
     __syncthreads();
@@ -784,7 +824,7 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
       __syncthreads();
     }
     // Linv = L^{-1}, one column per thread (forward substitution on the
-    // identity); its upper triangle is zero (read by Z = Linv O below)
+    // identity); its upper triangle is zero (read by the products below)
     for (int cc = tid; cc < MG; cc += nth) {
       for (int r = 0; r < cc; ++r) Li[r * MG + cc] = 0.0;
       for (int r = cc; r < MG; ++r) {
@@ -845,16 +885,6 @@ zgroup_factor_kernel(const DevMesh m, const int4 *__restrict__ glines, const lon
       Ld[LP + 8 * MG + q] = acc;
     }
     __syncthreads();
-    if (s + 1 < S) {  // Z_{s+1} = Linv_s O_s, O_s block diagonal over the lines
-      for (int q = tid; q < MG * MG; q += nth) {
-        const int r = q / MG, cc = q - r * MG, t2 = cc / M, c2 = cc - t2 * M;
-        const double *O = blk + (((size_t)lid[t2] * S + s) * 2 + 1) * M * M;
-        double acc = 0.0;
-        for (int p = 0; p < M; ++p) acc += Li[r * MG + t2 * M + p] * O[p * M + c2];
-        Z[q] = acc;
-      }
-      __syncthreads();
-    }
   }
 }
 
@@ -1359,20 +1389,39 @@ cudaError_t solve_batch_n(int prec, const DevMesh *meshes, const int2 *work, int
 }
 
 template <int N>
-cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
-                           const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
-                           double *fac64, int *status, cudaStream_t st) {
+cudaError_t zgroup_setup_n(const DevMesh &m, const ZGroupPlan &p, const ZGroupDev &gd, int inst,
+                           const int4 *lines, const long long *fac_off, double *blk, double *xblk, double *work,
+                           float *fac, double *fac64, int *status, cudaStream_t st) {
   zline_blocks_kernel<N><<<m.E, ((N * N + 31) / 32) * 32, 0, st>>>(m, blk);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   zgroup_cross_kernel<N><<<m.E, ((4 * N + 31) / 32) * 32, 0, st>>>(m, xblk);
   err = cudaGetLastError();
+  // the four group sizes at once, each with its own scratch: the 4-line
+  // groups (few, long) on st, the others on side streams forked from it
+  if (err == cudaSuccess) err = cudaEventRecord(gd.fork, st);
+  size_t off = 0;
+  bool used[3] = {false, false, false};
   for (int g = 1; g <= 4 && err == cudaSuccess; ++g) {
     const int cnt = p.inst_n[(size_t)inst * 5 + g];
     if (!cnt) continue;
-    zgroup_factor_kernel<N><<<cnt, 128, 0, st>>>(m, lines, fac_off, p.inst_start[(size_t)inst * 5 + g], g, blk,
-                                                 xblk, work, fac, fac64, status);
+    cudaStream_t sg = st;
+    if (g < 4) {
+      sg = gd.side[g - 1];
+      err = cudaStreamWaitEvent(sg, gd.fork, 0);
+      used[g - 1] = true;
+      if (err != cudaSuccess) break;
+    }
+    zgroup_factor_kernel<N><<<cnt, 128, 0, sg>>>(m, lines, fac_off, p.inst_start[(size_t)inst * 5 + g], g, blk,
+                                                 xblk, work + off, fac, fac64, status);
     err = cudaGetLastError();
+    const size_t MG = (size_t)g * 3 * N;
+    off += (size_t)cnt * 3 * MG * MG;
+  }
+  for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+    if (!used[k]) continue;
+    err = cudaEventRecord(gd.join[k], gd.side[k]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, gd.join[k], 0);
   }
   return err;
 }
@@ -1560,21 +1609,20 @@ size_t tn_zgroup_cross_bytes(const DevMesh &m) {
 }
 
 size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p, int inst) {
-  size_t mx = 0;
+  size_t sum = 0;
   for (int g = 1; g <= 4; ++g) {
     const size_t MG = (size_t)g * 3 * m.N;
-    const size_t b = (size_t)p.inst_n[(size_t)inst * 5 + g] * 3 * MG * MG * sizeof(double);
-    mx = b > mx ? b : mx;
+    sum += (size_t)p.inst_n[(size_t)inst * 5 + g] * 3 * MG * MG * sizeof(double);
   }
-  return mx;
+  return sum;
 }
 
-cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
-                            const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
-                            double *fac64, int *status, cudaStream_t st) {
+cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, const ZGroupDev &gd, int inst,
+                            const int4 *lines, const long long *fac_off, double *blk, double *xblk, double *work,
+                            float *fac, double *fac64, int *status, cudaStream_t st) {
   switch (m.N) {
 #define TN_CASE(NN) \
-    case NN: return zgroup_setup_n<NN>(m, p, inst, lines, fac_off, blk, xblk, work, fac, fac64, status, st);
+    case NN: return zgroup_setup_n<NN>(m, p, gd, inst, lines, fac_off, blk, xblk, work, fac, fac64, status, st);
     TN_CASE(3) TN_CASE(4) TN_CASE(5) TN_CASE(6) TN_CASE(7) TN_CASE(8) TN_CASE(9)
 #undef TN_CASE
     default: return cudaErrorInvalidValue;

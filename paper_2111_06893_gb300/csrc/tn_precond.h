@@ -71,10 +71,12 @@ bool tn_zgroup_plan(const tn::HostMesh *const *hms, int n, ZGroupPlan *plan, cha
 size_t tn_zgroup_cross_bytes(const DevMesh &m);                                // FP64 cross-line blocks (set-up)
 size_t tn_zgroup_work_bytes(const DevMesh &m, const ZGroupPlan &p, int inst);  // FP64 scratch (set-up)
 // factors of mirror `inst` (its mesh m); blk: tn_zline_block_bytes(m);
-// fac / fac64: plan.nfac entries; *status = 1 on a non-positive pivot
-cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, int inst, const int4 *lines,
-                            const long long *fac_off, double *blk, double *xblk, double *work, float *fac,
-                            double *fac64, int *status, cudaStream_t st);
+// fac / fac64: plan.nfac entries; *status = 1 on a non-positive pivot.  The
+// group sizes factor at once on st and gd's first three side streams
+// (forked from and joined back into st with gd's events).
+cudaError_t tn_zgroup_setup(const DevMesh &m, const ZGroupPlan &p, const ZGroupDev &gd, int inst,
+                            const int4 *lines, const long long *fac_off, double *blk, double *xblk, double *work,
+                            float *fac, double *fac64, int *status, cudaStream_t st);
 // as tn_zline_solve, over the groups (m: the mesh, nullptr for a batch);
 // partial sums: one per group.  q != nullptr: r -= alpha q first, as a
 // launch of its own over all gd.ndof unknowns
