@@ -48,3 +48,23 @@ def test_noalloc_rejects_meshes_beyond_its_limit():
     st = lib.tn_layer_energies_noalloc(ctx._h, C.c_void_p(u.data_ptr()), U.ctypes.data_as(C.POINTER(C.c_double)))
     assert st == thermonoise.TN_EINVAL_CODE
     assert b"at most 65536 elements" in lib.tn_last_error()
+
+
+def test_noalloc_energies_at_the_element_limit():
+    """A mesh of exactly 65536 elements (128 x 128 columns, four slabs of two
+    materials): the per-element scratch is full and the layer sums sit right
+    after it."""
+    from paper_2111_06893_gb300 import thermonoise
+    lib = thermonoise.load()
+    xb = [float(i) / 16.0 for i in range(129)]
+    desc = W.box(xb, xb, [0.0, -0.05, -0.1, -1.0, -4.0], 2, None, r0=2.0, slab_layer=[0, 0, 1, 1],
+                 materials=[W.COATING_HIGH, W.FUSED_SILICA])
+    ctx = thermonoise.setup(desc)
+    assert ctx.ndof == 3 * 27 * 65536
+    dp = C.POINTER(C.c_double)
+    u = torch.tensor(W.random_field(desc, 5), dtype=torch.float64, device="cuda")
+    U_ref = ctx.layer_energies(u)
+    U = np.zeros(2)
+    st = lib.tn_layer_energies_noalloc(ctx._h, C.c_void_p(u.data_ptr()), U.ctypes.data_as(dp))
+    assert st == thermonoise.TN_OK, lib.tn_last_error().decode()
+    assert np.max(np.abs(U - U_ref) / np.abs(U_ref)) < 1e-12, (U, U_ref)
