@@ -936,15 +936,20 @@ __device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ float warp_allsum(float v) {
+// three warp-wide sums at once: the three butterflies interleaved level by
+// level, so that their shuffles overlap instead of running one sum after
+// the other (every lane gets the three sums)
+template <typename T>
+__device__ __forceinline__ void warp_allsum3(T &a, T &b, T &c) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_allsum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 16; o > 0; o >>= 1) {
+    const T a2 = __shfl_xor_sync(0xffffffffu, a, o);
+    const T b2 = __shfl_xor_sync(0xffffffffu, b, o);
+    const T c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    a += a2;
+    b += b2;
+    c += c2;
+  }
 }
 
 // z = A_GG^{-1} r on group grp by the slot of G warps starting at warp w0;
@@ -1103,9 +1108,8 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, const
     T bv = rv;
     if (s > 0) {  // bv -= (O_{s-1}^T w_{s-1})_t, line by line
       const T x0 = XY[0], x1 = XY[1], x2 = XY[2];
-      const T s0 = warp_allsum(act ? XY[4] * w : T(0));
-      const T s1 = warp_allsum(act ? XY[5] * w : T(0));
-      const T s2 = warp_allsum(act ? XY[6] * w : T(0));
+      T s0 = act ? XY[4] * w : T(0), s1 = act ? XY[5] * w : T(0), s2 = act ? XY[6] * w : T(0);
+      warp_allsum3(s0, s1, s2);
       T o = x0 * __shfl_sync(0xffffffffu, w, 0) + x1 * __shfl_sync(0xffffffffu, w, N) +
             x2 * __shfl_sync(0xffffffffu, w, 2 * N);
       if (k == N - 1) o += a == 0 ? s0 : (a == 1 ? s1 : s2);
@@ -1136,9 +1140,8 @@ __device__ __forceinline__ void zg_slot(int grp, int w0, int mncol, int S, const
       const T e0 = __shfl_sync(0xffffffffu, x, N - 1);
       const T e1 = __shfl_sync(0xffffffffu, x, 2 * N - 1);
       const T e2 = __shfl_sync(0xffffffffu, x, 3 * N - 1);
-      const T c0 = warp_allsum(act ? XY[0] * x : T(0));
-      const T c1 = warp_allsum(act ? XY[1] * x : T(0));
-      const T c2 = warp_allsum(act ? XY[2] * x : T(0));
+      T c0 = act ? XY[0] * x : T(0), c1 = act ? XY[1] * x : T(0), c2 = act ? XY[2] * x : T(0);
+      warp_allsum3(c0, c1, c2);
       if (lane < 6) vb(par)[32 * li + lane] = lane < 3 ? (lane == 0 ? e0 : (lane == 1 ? e1 : e2))
                                                       : (lane == 3 ? c0 : (lane == 4 ? c1 : c2));
       sync();
