@@ -60,7 +60,7 @@ def fp32_apply_flops_per_dof(N):
 # from `ncu --set full -k regex:zgroup_packed_kernel` of `bench.py --mode
 # apply --workload single_coating`; absent where no capture of the current
 # kernel exists
-ZLINE_TRAFFIC = {("single_coating", "zgroup_packed_kernel<7,float>"): 342373120.0 + 10122240.0}
+ZLINE_TRAFFIC = {("single_coating", "zgroup_packed_kernel<7,float>"): 342619136.0 + 10593280.0}
 
 
 # DRAM bytes (read + write) of one FP32 apply per occupancy variant, from
