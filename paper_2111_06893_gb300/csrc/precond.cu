@@ -688,7 +688,8 @@ __global__ void zgroup_cross_kernel(const DevMesh m, double *__restrict__ xblk) 
 
 // Group record of slab s: [S_s^{-1} packed by columns (lower triangle,
 // zlp(MG)) | O_{s-1} in factored form (8 MG) | W_s], S_s = L_s L_s^T the
-// slab's Schur complement of the block Cholesky (S_s^{-1} = Linv_s^T Linv_s).  The coupling block O_{s-1} (rows: slab s - 1,
+// slab's Schur complement of the block Cholesky (S_s^{-1} = Linv_s^T
+// Linv_s).  The coupling block O_{s-1} (rows: slab s - 1,
 // columns: slab s, block diagonal over the lines) is nonzero only in the
 // rows of the bottom-face nodes (k = 0) and the columns of the top-face
 // nodes (k2 = N - 1) of each line (Eqs. (numflux), (penalty) on the zeta
